@@ -1,0 +1,70 @@
+"""Deflated sign(Q) and the Neuberger-Dirac operator D_N of the oracle (plain numpy, FP64).
+
+Test infrastructure only.
+  D_N = (1 + gamma5 sign(Q)) / abar  (Sec. 2.2), with abar = a / (1 + s), a = 1, so
+  1/abar = 1 + s; Q = gamma5 D_W with D_W's mass m = -1 - s gives the paper's
+  Q = gamma5 (a D_W - 1 - s).  (abar is not defined in the paper itself; this value is the
+  one for which the paper's error bound (2/abar)(1 - abar m/2) equals (2/a)(1 + s - am/2).)
+  Massive operator: D_N^m = (1 - abar m_q / 2) D_N + m_q.
+  Deflated sign (Sec. 2.3, the formula replacing the polynomial approximation):
+     sign(Q) ~ P_+ - P_- + (1 - P_+ - P_-) X R(X^2),  X = Q / ||Q||,
+  with R the Zolotarev rational function (oracle/zolotarev.py) in place of P_n.
+  Reading: the projector is applied on both sides, (1 - P) X R(X^2) (1 - P), which equals
+  the paper's form when V is an exact invariant subspace and keeps the approximation
+  Hermitian; ``two_sided=False`` gives the paper's literal left-only form.
+  ||Q||^2 is passed in as lam_max (an upper estimate of lambda_max(Q^2)); eps is the lower
+  end of the approximation interval of X^2.
+"""
+import numpy as np
+
+from . import mscg, wilson, zolotarev
+
+_zcache = {}
+
+
+def zolo(npoles, eps):
+    key = (int(npoles), float(eps))
+    if key not in _zcache:
+        _zcache[key] = zolotarev.zolotarev(int(npoles), float(eps))
+    return _zcache[key]
+
+
+def gamma5(psi):
+    out = psi.copy()
+    out[..., 2:, :] *= -1.0
+    return out
+
+
+def sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u=None, nu=None, two_sided=True,
+               antiperiodic_t=False, maxit=100000):
+    """sign(Q) eta with l = len(nu) deflated modes (u orthonormal, Q u_k ~ nu_k u_k)."""
+    Q = lambda v: wilson.apply_Q(U, np.ascontiguousarray(v), dims, m, antiperiodic_t)
+    coef = zolo(npoles, eps)
+    l = 0 if nu is None else len(nu)
+    if l:
+        c = np.array([np.vdot(u[k], eta) for k in range(l)])
+        eta_perp = eta - np.einsum("k,k...->...", c, u)
+    else:
+        c = np.zeros(0, dtype=np.complex128)
+        eta_perp = eta
+    src = eta_perp if (two_sided or not l) else eta
+    lam_min = eps if (two_sided or not l) else float(np.min(np.asarray(nu) ** 2)) / lam_max
+    tols = mscg.rational_tolerances(coef["b"], coef["sigma"], lam_min, tol)
+    x, info = mscg.multishift_cg(lambda v: Q(Q(v)) / lam_max, src, coef["sigma"], tols, maxit=maxit)
+    y = np.einsum("l,l...->...", np.asarray(coef["b"]), x)
+    z = Q(y) / np.sqrt(lam_max)
+    if l:
+        cz = np.array([np.vdot(u[k], z) for k in range(l)])
+        z = z - np.einsum("k,k...->...", cz, u) + np.einsum("k,k...->...", np.sign(nu) * c, u)
+    info = dict(info)
+    info["delta"] = coef["delta"]
+    return z, info
+
+
+def dn_apply(U, dims, m, s, eta, lam_max, eps, npoles, tol, u=None, nu=None, m_q=0.0, two_sided=True,
+             antiperiodic_t=False):
+    """D_N^m eta = (1 - abar m_q/2) (1 + s) (eta + gamma5 sign(Q) eta) + m_q eta."""
+    sg, info = sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u, nu, two_sided, antiperiodic_t)
+    abar = 1.0 / (1.0 + s)
+    dn = (eta + gamma5(sg)) / abar
+    return (1.0 - abar * m_q / 2.0) * dn + m_q * eta, info
