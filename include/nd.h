@@ -1,0 +1,221 @@
+/*
+ * nd.h -- C-ABI of libnd: the Neuberger-Dirac operator on one GB300 (sm_103a).
+ *
+ * Walk, Wittig, Dranischnikow, Schomer, "Implementation of the Neuberger-Dirac operator
+ * on GPUs" (Lattice 2010).  Section numbers below refer to that paper.
+ *
+ * Conventions shared by every call
+ *   Lattice extents dims = {T, L1, L2, L3}, all even; site x = (x0,x1,x2,x3), mu = 0 is time.
+ *   lex(x) = x3 + L3*(x2 + L2*(x1 + L1*x0)); V = T*L1*L2*L3.
+ *   Canonical (boundary) layouts, FP64 with interleaved (re, im):
+ *     spinor  psi[lex][spin 4][colour 3][2]                 12 complex per site
+ *     links   U[mu][lex][row 3][col 3][2]                    U_mu(x), row-major
+ *     force   F[mu][lex][a = 1..8]                           coefficient of T^a = lambda^a/2
+ *   Gamma matrices: chiral basis, gamma5 = gamma0 gamma1 gamma2 gamma3 = diag(1,1,-1,-1);
+ *   in 2x2 blocks gamma0 = [[0,-1],[-1,0]], gamma_k = [[0,-i sigma_k],[i sigma_k,0]].
+ *   Boundary conditions periodic; optionally antiperiodic in time.
+ *   Internal layouts (opaque to the caller, sized by nd_spinor_bytes): even-odd ordered
+ *   structure-of-arrays, eo(x) = p(x)*V/2 + lex(x)/2 with p(x) = (x0+x1+x2+x3) mod 2.
+ *
+ * Ownership and errors
+ *   Every pointer argument named *_dev is device memory owned by the caller; the library
+ *   never frees or keeps it beyond the call.  The context owns its own device copies of the
+ *   links, its workspaces and its low-mode basis, and frees them in nd_destroy.
+ *   All GPU work is ordered on the context's stream.  Calls that return host values
+ *   (info structs, host arrays) synchronise that stream before returning.
+ *   Every call returns an nd_status; nothing is thrown across the ABI.  On failure the
+ *   context keeps a readable message (nd_last_error).  After ND_ERR_CUDA the context is
+ *   unusable (ND_ERR_STATE) and must be destroyed.
+ *   The library fails loudly (ND_ERR_CUDA) when no CUDA device is present: there is no
+ *   CPU fallback.
+ */
+#ifndef ND_H
+#define ND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nd_ctx nd_ctx;
+
+typedef enum {
+  ND_OK = 0,
+  ND_ERR_INVALID_ARG = -1,   /* bad sizes, odd extents, null pointers, unsupported combination */
+  ND_ERR_CUDA = -2,          /* a CUDA call failed; the message names it */
+  ND_ERR_OOM = -3,           /* device allocation failed */
+  ND_ERR_NOT_CONVERGED = -4, /* iteration limit reached; outputs hold the last iterate, info is filled */
+  ND_ERR_BREAKDOWN = -5,     /* (p, A p) <= 0 or a zero pivot in a Krylov recurrence */
+  ND_ERR_NAN = -6,           /* a norm became NaN or Inf */
+  ND_ERR_STATE = -7          /* call out of order (e.g. no links set) or context poisoned */
+} nd_status;
+
+typedef enum {
+  ND_FP64 = 0, /* FP64 storage and arithmetic */
+  ND_FP32 = 1, /* FP32 storage and arithmetic, FP64 global reductions */
+  ND_FP16 = 2  /* FP16 storage with one FP32 scale per site, FP32 arithmetic, FP64 reductions */
+} nd_prec;
+
+typedef enum {
+  ND_RECON_NONE = 0, /* do not keep links in this precision */
+  ND_RECON_8 = 8,    /* 8 reals: a2, a3, b1, arg a1, arg c1 (Sec. 2.1, 8-parameter form) */
+  ND_RECON_12 = 12,  /* 12 reals: columns a, b; c = (a x b)^* rebuilt in registers (Sec. 2.1) */
+  ND_RECON_18 = 18   /* all 18 reals */
+} nd_recon;
+
+/* ---------------------------------------------------------------- lifecycle */
+
+/* Create a context for one lattice.  m is the Wilson bare mass of D_W (Sec. 2.1); s is the
+ * overlap parameter of Sec. 2.2 (D_N = (1 + s)(1 + gamma5 sign Q), abar = 1/(1 + s)).
+ * stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: ND_ERR_INVALID_ARG for odd or non-positive extents or |s| >= 1; ND_ERR_CUDA when no
+ * device is usable. */
+nd_status nd_create(nd_ctx** ctx, const int dims[4], int antiperiodic_t, double m, double s, void* stream);
+void nd_destroy(nd_ctx* ctx);
+nd_status nd_set_stream(nd_ctx* ctx, void* stream);
+const char* nd_status_string(nd_status st);
+const char* nd_last_error(const nd_ctx* ctx);
+/* Lattice volume and bytes of one internal spinor field of the given precision. */
+int64_t nd_volume(const nd_ctx* ctx);
+size_t nd_spinor_bytes(const nd_ctx* ctx, nd_prec prec);
+
+/* ---------------------------------------------------------------- fields */
+
+/* Copy the canonical FP64 gauge field U_dev ([4][V][3][3][2], device) into the context and
+ * compress it, for each precision p, to recon[p] reals per link (ND_RECON_NONE skips p).
+ * The 8-real form is singular when |a1| = 1 (e.g. unit links); such a field returns
+ * ND_ERR_INVALID_ARG for recon 8.  Follows Sec. 2.1 (link storage). */
+nd_status nd_set_links(nd_ctx* ctx, const double* U_dev, const int recon[3]);
+
+/* Canonical FP64 spinors (nrhs consecutive fields, device) <-> internal layout of precision
+ * prec (nrhs consecutive fields of nd_spinor_bytes each, device). */
+nd_status nd_pack_spinor(nd_ctx* ctx, void* internal_dev, const double* canon_dev, nd_prec prec, int nrhs);
+nd_status nd_unpack_spinor(nd_ctx* ctx, double* canon_dev, const void* internal_dev, nd_prec prec, int nrhs);
+
+/* Export the GPU's site tables: lex2eo_dev[V] (eo index of each lex site) and
+ * nbr_dev[8][V] (eo index of the neighbour of eo site e in direction d = 2*mu + s,
+ * s = 0 for x + mu, 1 for x - mu), both int32, device. */
+nd_status nd_eo_tables(nd_ctx* ctx, int32_t* lex2eo_dev, int32_t* nbr_dev);
+
+/* ---------------------------------------------------------------- operator Q */
+
+/* out = Q in = gamma5 D_W in (Sec. 2.1) on nrhs internal fields of precision prec, with
+ *   D_W phi(x) = (4+m) phi(x) - 1/2 sum_{mu=+-0..+-3} U_mu(x) (1 - gamma_mu) phi(x+mu).
+ * out and in must not overlap.  Links must be set in precision prec. */
+nd_status nd_apply_Q(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec, int nrhs);
+
+/* Even-odd block of Q for one output parity (the half pass of an even-odd preconditioned
+ * operator): out_p = gamma5 [ diag_coef * in_p - 1/2 sum_mu (hops from in_{1-p}) ].
+ * diag_coef = 4+m gives the rows of Q of parity p; diag_coef = 0 gives the pure hopping
+ * block (in_p is then not read).  Only the parity-p half of out is written. */
+nd_status nd_apply_Q_parity(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec, int parity,
+                            double diag_coef);
+
+/* Convenience: Q on canonical FP64 device spinors (packs, applies in FP64, unpacks). */
+nd_status nd_apply_Q_canonical(nd_ctx* ctx, double* out_dev, const double* in_dev);
+
+/* ---------------------------------------------------------------- solvers */
+
+typedef struct {
+  int iters;             /* Krylov iterations of the (last) multi-shift pass */
+  int outer;             /* outer defect-correction steps (mixed precision), else 0 */
+  int sloppy_iters;      /* total sloppy-precision iterations including refinement */
+  double max_resid;      /* max over shifts of the true FP64 relative residual */
+  double time_ms;
+} nd_solve_info;
+
+/* Solve (Q^2 + shifts[k]) x_k = b for k < n (multi-shift CG, one Krylov space; each shift
+ * stops at relative residual tol).  b_dev and x_dev[k] are canonical FP64 device spinors;
+ * x_dev is a host array of n device pointers.  inner = ND_FP64 runs everything in FP64;
+ * ND_FP32 / ND_FP16 run the Krylov iterations in that storage precision with FP64
+ * reductions and refine every shift in FP64 (defect correction) down to tol.
+ * Requires Q^2 + shifts[k] > 0 (shifts >= 0 and Q invertible, or shifts > 0). */
+nd_status nd_solve(nd_ctx* ctx, double* const* x_dev, const double* b_dev, const double* shifts, int n,
+                   double tol, int maxit, nd_prec inner, nd_solve_info* info);
+
+/* ---------------------------------------------------------------- low modes (Sec. 2.3) */
+
+typedef struct {
+  int l;                  /* number of modes kept */
+  int iters;              /* Q^2 applications spent */
+  double lambda_max;      /* estimate of the largest eigenvalue of Q^2 */
+  double lambda_next;     /* estimate of lambda_{l+1}(Q^2) */
+  double kappa_plus;      /* kappa_+ of Sec. 2.3 */
+  double kappa_minus;     /* kappa_- of Sec. 2.3 */
+  double max_rho;         /* max_k rho_k = ||(Q - nu_k) u_k|| */
+  double time_ms;
+} nd_lowmode_info;
+
+/* Compute the l lowest modes of Q^2 in FP64 (thick-restart Lanczos), then the Rayleigh-Ritz
+ * eigenpairs (nu_k, u_k) of Q on their span, the residues rho_k and kappa_+- (Sec. 2.3).
+ * The basis stays in the context for nd_apply_DN.  Host outputs (may be NULL):
+ * nu[l], rho[l], eval_Q2[l+1] (the Lanczos eigenvalues of Q^2, ascending).
+ * Converges each of the l+1 lowest Ritz values of Q^2 to relative residual tol. */
+nd_status nd_lowmodes(nd_ctx* ctx, int l, double tol, int maxit, double* nu, double* rho, double* eval_Q2,
+                      nd_lowmode_info* info);
+
+/* Replace the context's low modes by caller-provided orthonormal vectors (canonical FP64,
+ * device, [l][V*12] complex) with their Q eigenvalues nu (host) and an estimate of
+ * lambda_{l+1}(Q^2) (host).  rho and kappa are recomputed on the GPU. */
+nd_status nd_set_lowmodes(nd_ctx* ctx, int l, const double* evecs_dev, const double* nu, double lambda_next,
+                          nd_lowmode_info* info);
+
+/* Copy the context's low modes out: evecs_dev [l][V*12] complex canonical (device), nu[l] (host). */
+nd_status nd_get_lowmodes(nd_ctx* ctx, double* evecs_dev, double* nu);
+
+/* Estimate lambda_max(Q^2) with iters Lanczos steps (upper Ritz value; not padded). */
+nd_status nd_lambda_max(nd_ctx* ctx, int iters, double* lambda_max);
+
+/* ---------------------------------------------------------------- sign(Q) and D_N (Sec. 2.2, 2.3) */
+
+/* Zolotarev coefficients of R(x) = x sum_l b_l / (x^2 + sigma_l) ~ sign(x) on sqrt(eps) <= |x| <= 1
+ * (host computation; n poles).  Returns the uniform error delta.  Host arrays sigma[n], b[n]. */
+nd_status nd_zolotarev(int n, double eps, double* sigma, double* b, double* delta);
+
+typedef struct {
+  int n_poles;         /* Zolotarev poles (shifted systems) */
+  double eps;          /* lower end of the X^2 interval; 0 = 0.99 * lambda_next / lambda_max */
+  double lambda_max;   /* ||Q||^2 estimate; 0 = 1.01 * Lanczos estimate */
+  double tol;          /* error target of the rational part (relative to ||source||) */
+  int maxit;           /* Krylov iteration limit per multi-shift pass */
+  nd_prec inner_prec;  /* ND_FP64: pure FP64; ND_FP32/ND_FP16: sloppy Krylov + FP64 refinement */
+  double m_q;          /* quark mass of D_N^m = (1 - abar m_q / 2) D_N + m_q (0 = massless) */
+  int left_only;       /* 1: the paper's literal (1 - P) X R(X^2) eta; 0: (1 - P) X R(X^2) (1 - P) eta */
+} nd_dn_params;
+
+typedef struct {
+  int iters;           /* Krylov iterations of the multi-shift pass */
+  int sloppy_iters;    /* total sloppy iterations including refinement */
+  int outer;           /* FP64 refinement sweeps */
+  int n_low;           /* deflated modes used */
+  double delta;        /* Zolotarev uniform error on [sqrt(eps), 1] */
+  double eps;          /* eps used */
+  double lambda_max;   /* lambda_max used */
+  double max_resid;    /* max over shifts of the FP64 relative residual of the shifted solves */
+  double time_ms;
+} nd_dn_info;
+
+/* out = sign(Q) in with the deflated Zolotarev approximation
+ *   sign(Q) ~ P_+ - P_- + (1 - P) X R(X^2) (1 - P),  X = Q / sqrt(lambda_max)   (Sec. 2.3),
+ * using the context's low modes (none if nd_lowmodes/nd_set_lowmodes was not called).
+ * in_dev/out_dev: canonical FP64 device spinors (may not overlap). */
+nd_status nd_apply_sign(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p, nd_dn_info* info);
+
+/* out = D_N^m in, D_N = (1 + gamma5 sign(Q)) / abar, abar = 1/(1 + s)  (Sec. 2.2, 2.3). */
+nd_status nd_apply_DN(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p, nd_dn_info* info);
+
+/* ---------------------------------------------------------------- differentiation */
+
+/* Force of S = phi^dagger (Q^2)^{-1} phi with respect to the links: F[mu][lex][a] =
+ * dS/d omega for U_mu(x) -> exp(i omega T^a) U_mu(x), T^a = lambda^a/2 (F_dev: [4][V][8]
+ * FP64, device).  X = (Q^2)^{-1} phi is recomputed by CG (inner precision as nd_solve) to
+ * relative residual tol; the force itself is one FP64 pass over the links. */
+nd_status nd_force(nd_ctx* ctx, double* F_dev, const double* phi_dev, double tol, int maxit, nd_prec inner,
+                   nd_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ND_H */

@@ -1,0 +1,310 @@
+"""Python binding of libnd: the Neuberger-Dirac operator on one GB300 (sm_103a).
+
+Argument marshalling only: every function below forwards to the C-ABI entry point of the
+same name declared in include/nd.h; all arithmetic runs in the library's CUDA kernels.
+PyTorch supplies device memory (tensor.data_ptr()) and the current CUDA stream.
+
+If libnd.so is missing or no CUDA device is present the calls raise: there is no CPU
+fallback.
+
+Canonical tensors (see include/nd.h): spinors complex128 [V, 4, 3] (or float64 [V, 4, 3, 2]),
+links complex128 [4, V, 3, 3], force float64 [4, V, 8], all on cuda and contiguous.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+ND_OK, ND_ERR_INVALID_ARG, ND_ERR_CUDA, ND_ERR_OOM = 0, -1, -2, -3
+ND_ERR_NOT_CONVERGED, ND_ERR_BREAKDOWN, ND_ERR_NAN, ND_ERR_STATE = -4, -5, -6, -7
+ND_FP64, ND_FP32, ND_FP16 = 0, 1, 2
+PRECS = {"fp64": ND_FP64, "fp32": ND_FP32, "fp16": ND_FP16}
+
+
+class NdError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class nd_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("sloppy_iters", ctypes.c_int),
+                ("max_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+class nd_lowmode_info(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("iters", ctypes.c_int), ("lambda_max", ctypes.c_double),
+                ("lambda_next", ctypes.c_double), ("kappa_plus", ctypes.c_double),
+                ("kappa_minus", ctypes.c_double), ("max_rho", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+class nd_dn_params(ctypes.Structure):
+    _fields_ = [("n_poles", ctypes.c_int), ("eps", ctypes.c_double), ("lambda_max", ctypes.c_double),
+                ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_prec", ctypes.c_int),
+                ("m_q", ctypes.c_double), ("left_only", ctypes.c_int)]
+
+
+class nd_dn_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("sloppy_iters", ctypes.c_int), ("outer", ctypes.c_int),
+                ("n_low", ctypes.c_int), ("delta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("lambda_max", ctypes.c_double), ("max_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+_P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
+_SIGS = {
+    "nd_create": ([ctypes.POINTER(_P), _P, _I, _D, _D, _P], _I),
+    "nd_destroy": ([_P], None),
+    "nd_set_stream": ([_P, _P], _I),
+    "nd_status_string": ([_I], ctypes.c_char_p),
+    "nd_last_error": ([_P], ctypes.c_char_p),
+    "nd_volume": ([_P], _L),
+    "nd_spinor_bytes": ([_P, _I], ctypes.c_size_t),
+    "nd_set_links": ([_P, _P, _P], _I),
+    "nd_pack_spinor": ([_P, _P, _P, _I, _I], _I),
+    "nd_unpack_spinor": ([_P, _P, _P, _I, _I], _I),
+    "nd_eo_tables": ([_P, _P, _P], _I),
+    "nd_apply_Q": ([_P, _P, _P, _I, _I], _I),
+    "nd_apply_Q_parity": ([_P, _P, _P, _I, _I, _D], _I),
+    "nd_apply_Q_canonical": ([_P, _P, _P], _I),
+    "nd_solve": ([_P, _P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
+    "nd_lowmodes": ([_P, _I, _D, _I, _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
+    "nd_set_lowmodes": ([_P, _I, _P, _P, _D, ctypes.POINTER(nd_lowmode_info)], _I),
+    "nd_get_lowmodes": ([_P, _P, _P], _I),
+    "nd_lambda_max": ([_P, _I, ctypes.POINTER(_D)], _I),
+    "nd_zolotarev": ([_I, _D, _P, _P, ctypes.POINTER(_D)], _I),
+    "nd_apply_sign": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
+    "nd_apply_DN": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
+    "nd_force": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
+}
+
+_lib = None
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libnd.so (building it first if it is missing and nvcc is available)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise NdError(ND_ERR_STATE, "libnd.so is not built (run __graft_entry__.build())")
+            _build.build()
+        L = ctypes.CDLL(_build.LIB)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    return sorted(_SIGS)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _check(ctx, st, what):
+    if st != ND_OK:
+        msg = lib().nd_last_error(ctx).decode() if ctx else lib().nd_status_string(st).decode()
+        raise NdError(st, f"{what}: {msg}")
+
+
+def _f64(t):
+    """Canonical tensors may be complex128; the C-ABI sees interleaved float64."""
+    import torch
+    assert t.is_cuda and t.is_contiguous(), "canonical tensors must be contiguous CUDA tensors"
+    assert t.dtype in (torch.complex128, torch.float64)
+    return t
+
+
+# ------------------------------------------------------------------ C-ABI wrappers (same names)
+
+def nd_create(dims, antiperiodic_t=False, m=-1.4, s=0.4, stream=None):
+    h = ctypes.c_void_p()
+    d = (ctypes.c_int * 4)(*[int(x) for x in dims])
+    st = lib().nd_create(ctypes.byref(h), ctypes.cast(d, ctypes.c_void_p), int(antiperiodic_t), float(m), float(s),
+                         stream if stream is not None else _stream())
+    _check(None, st, "nd_create")
+    return h
+
+
+def nd_destroy(ctx):
+    lib().nd_destroy(ctx)
+
+
+def nd_set_stream(ctx, stream=None):
+    _check(ctx, lib().nd_set_stream(ctx, stream if stream is not None else _stream()), "nd_set_stream")
+
+
+def nd_volume(ctx):
+    return int(lib().nd_volume(ctx))
+
+
+def nd_spinor_bytes(ctx, prec):
+    return int(lib().nd_spinor_bytes(ctx, int(prec)))
+
+
+def nd_set_links(ctx, U, recon=(18, 18, 12)):
+    r = (ctypes.c_int * 3)(*[int(x) for x in recon])
+    _check(ctx, lib().nd_set_links(ctx, _ptr(_f64(U)), ctypes.cast(r, ctypes.c_void_p)), "nd_set_links")
+
+
+def nd_pack_spinor(ctx, internal, canon, prec, nrhs=1):
+    _check(ctx, lib().nd_pack_spinor(ctx, _ptr(internal), _ptr(_f64(canon)), int(prec), int(nrhs)), "nd_pack_spinor")
+
+
+def nd_unpack_spinor(ctx, canon, internal, prec, nrhs=1):
+    _check(ctx, lib().nd_unpack_spinor(ctx, _ptr(_f64(canon)), _ptr(internal), int(prec), int(nrhs)),
+           "nd_unpack_spinor")
+
+
+def nd_eo_tables(ctx, lex2eo, nbr):
+    _check(ctx, lib().nd_eo_tables(ctx, _ptr(lex2eo), _ptr(nbr)), "nd_eo_tables")
+
+
+def nd_apply_Q(ctx, out, inp, prec, nrhs=1):
+    _check(ctx, lib().nd_apply_Q(ctx, _ptr(out), _ptr(inp), int(prec), int(nrhs)), "nd_apply_Q")
+
+
+def nd_apply_Q_parity(ctx, out, inp, prec, parity, diag_coef):
+    _check(ctx, lib().nd_apply_Q_parity(ctx, _ptr(out), _ptr(inp), int(prec), int(parity), float(diag_coef)),
+           "nd_apply_Q_parity")
+
+
+def nd_apply_Q_canonical(ctx, out, inp):
+    _check(ctx, lib().nd_apply_Q_canonical(ctx, _ptr(_f64(out)), _ptr(_f64(inp))), "nd_apply_Q_canonical")
+
+
+def nd_solve(ctx, xs, b, shifts, tol, maxit=100000, inner=ND_FP64):
+    n = len(shifts)
+    xp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+    sh = (ctypes.c_double * n)(*[float(s) for s in shifts])
+    info = nd_solve_info()
+    st = lib().nd_solve(ctx, ctypes.cast(xp, ctypes.c_void_p), _ptr(_f64(b)), ctypes.cast(sh, ctypes.c_void_p), n,
+                        float(tol), int(maxit), int(inner), ctypes.byref(info))
+    _check(ctx, st, "nd_solve")
+    return info
+
+
+def nd_lowmodes(ctx, l, tol=1e-12, maxit=100000):
+    nu = (ctypes.c_double * l)()
+    rho = (ctypes.c_double * l)()
+    ev = (ctypes.c_double * (l + 1))()
+    info = nd_lowmode_info()
+    st = lib().nd_lowmodes(ctx, int(l), float(tol), int(maxit), ctypes.cast(nu, _P), ctypes.cast(rho, _P),
+                           ctypes.cast(ev, _P), ctypes.byref(info))
+    _check(ctx, st, "nd_lowmodes")
+    return list(nu), list(rho), list(ev), info
+
+
+def nd_set_lowmodes(ctx, evecs, nu, lambda_next):
+    l = len(nu)
+    nuc = (ctypes.c_double * l)(*[float(x) for x in nu])
+    info = nd_lowmode_info()
+    st = lib().nd_set_lowmodes(ctx, l, _ptr(_f64(evecs)), ctypes.cast(nuc, _P), float(lambda_next), ctypes.byref(info))
+    _check(ctx, st, "nd_set_lowmodes")
+    return info
+
+
+def nd_get_lowmodes(ctx, evecs, l):
+    nu = (ctypes.c_double * l)()
+    _check(ctx, lib().nd_get_lowmodes(ctx, _ptr(_f64(evecs)), ctypes.cast(nu, _P)), "nd_get_lowmodes")
+    return list(nu)
+
+
+def nd_lambda_max(ctx, iters=50):
+    v = ctypes.c_double()
+    _check(ctx, lib().nd_lambda_max(ctx, int(iters), ctypes.byref(v)), "nd_lambda_max")
+    return v.value
+
+
+def nd_zolotarev(n, eps):
+    sig = (ctypes.c_double * n)()
+    b = (ctypes.c_double * n)()
+    d = ctypes.c_double()
+    st = lib().nd_zolotarev(int(n), float(eps), ctypes.cast(sig, _P), ctypes.cast(b, _P), ctypes.byref(d))
+    _check(None, st, "nd_zolotarev")
+    return list(sig), list(b), d.value
+
+
+def dn_params(n_poles=16, eps=0.0, lambda_max=0.0, tol=1e-12, maxit=100000, inner_prec=ND_FP64, m_q=0.0,
+              left_only=False):
+    return nd_dn_params(int(n_poles), float(eps), float(lambda_max), float(tol), int(maxit), int(inner_prec),
+                        float(m_q), int(left_only))
+
+
+def nd_apply_sign(ctx, out, inp, params):
+    info = nd_dn_info()
+    _check(ctx, lib().nd_apply_sign(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params), ctypes.byref(info)),
+           "nd_apply_sign")
+    return info
+
+
+def nd_apply_DN(ctx, out, inp, params):
+    info = nd_dn_info()
+    _check(ctx, lib().nd_apply_DN(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params), ctypes.byref(info)),
+           "nd_apply_DN")
+    return info
+
+
+def nd_force(ctx, F, phi, tol=1e-12, maxit=100000, inner=ND_FP64):
+    info = nd_solve_info()
+    _check(ctx, lib().nd_force(ctx, _ptr(F), _ptr(_f64(phi)), float(tol), int(maxit), int(inner), ctypes.byref(info)),
+           "nd_force")
+    return info
+
+
+# ------------------------------------------------------------------ convenience object
+
+class Lattice:
+    """Owns one nd_ctx; holds links and hands out internal spinor buffers as torch tensors."""
+
+    def __init__(self, dims, U=None, m=-1.4, s=0.4, antiperiodic_t=False, recon=(18, 18, 12)):
+        import torch
+        self.dims = tuple(int(d) for d in dims)
+        self.m, self.s = m, s
+        self.ctx = nd_create(self.dims, antiperiodic_t, m, s)
+        self.V = nd_volume(self.ctx)
+        if U is not None:
+            self.set_links(U, recon)
+
+    def set_links(self, U, recon=(18, 18, 12)):
+        nd_set_links(self.ctx, U, recon)
+
+    def field(self, prec, nrhs=1):
+        import torch
+        nbytes = nd_spinor_bytes(self.ctx, prec) * nrhs
+        return torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+    def pack(self, canon, prec, nrhs=1):
+        f = self.field(prec, nrhs)
+        nd_pack_spinor(self.ctx, f, canon, prec, nrhs)
+        return f
+
+    def unpack(self, internal, prec, nrhs=1):
+        import torch
+        out = torch.empty((nrhs, self.V, 4, 3) if nrhs > 1 else (self.V, 4, 3), dtype=torch.complex128, device="cuda")
+        nd_unpack_spinor(self.ctx, out, internal, prec, nrhs)
+        return out
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            nd_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,38 @@
+// Dispatch of Q launches to the per-precision translation units.
+#include <cstdlib>
+
+#include "kernels.h"
+
+namespace nd {
+cudaError_t launch_q_fp64(const Geom& g, const QLaunch& L, cudaStream_t st);
+cudaError_t launch_q_fp32(const Geom& g, const QLaunch& L, cudaStream_t st);
+cudaError_t launch_q_fp16(const Geom& g, const QLaunch& L, cudaStream_t st);
+
+// Warps per site for a (precision, link form).  ND_Q_SPLIT=1|2|4 in the environment overrides
+// the choice (used by the tuning sweep).
+int default_split(int prec, int recon, bool half) {
+  (void)recon;
+  static int env = -1;
+  if (env < 0) {
+    const char* e = std::getenv("ND_Q_SPLIT");
+    env = e ? std::atoi(e) : 0;
+    if (env != 1 && env != 2 && env != 4) env = 0;
+  }
+  if (env) return env;
+  // measured on 64x32^3: one warp per site is fastest for FP64 and FP32; FP16 gains from two
+  // warps per site on the one-parity pass only
+  return (prec == 2 && half) ? 2 : 1;
+}
+
+cudaError_t launch_q(const Geom& g, const QLaunch& L0, cudaStream_t st) {
+  if (L0.nsites <= 0) return cudaSuccess;
+  QLaunch L = L0;
+  if (L.split == 0) L.split = default_split(L.prec, L.recon, L.nsites != 2 * g.Vh);
+  switch (L.prec) {
+    case 0: return launch_q_fp64(g, L, st);
+    case 1: return launch_q_fp32(g, L, st);
+    case 2: return launch_q_fp16(g, L, st);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace nd

@@ -1,0 +1,6 @@
+// Instantiations of the Q kernels for storage precision FP32 (see dslash_impl.cuh).
+#include "dslash_impl.cuh"
+
+namespace nd {
+cudaError_t launch_q_fp32(const Geom& g, const QLaunch& L, cudaStream_t st) { return launch_q1<P32>(g, L, st); }
+}  // namespace nd

@@ -1,0 +1,193 @@
+// Kernels applying Q = gamma5 D_W (Sec. 2.1) on the even-odd ordered lattice.
+//
+// Work split: each output site is handled by SPLIT warps-parts (SPLIT = 1, 2 or 4); part k
+// computes the hops of directions mu with mu % SPLIT == k (forward and backward) for 32
+// consecutive sites.  Parts are whole warps, so no branch diverges inside a warp; the partial
+// accumulators are summed through shared memory in a fixed order, so every part holds the
+// identical full sum.  Part k then stores the output chunks it owns (chunk c with
+// c % SPLIT == k).  Splitting lowers registers per thread and multiplies the number of
+// independent loads in flight per SM, which is what a bandwidth-bound stencil needs.
+// Epilogue: gamma5 and the diagonal (4+m) fused; optional y-term, fused FP64 norms, and the
+// fused CG residual update of the multi-shift solver.
+#pragma once
+#include "dslash.cuh"
+#include "kernels.h"
+#include "reduce.cuh"
+
+namespace nd {
+
+constexpr int Q_THREADS = 256;
+
+template <int P, int R, int SPLIT>
+__device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& acc, const Geom& g, const Site& s,
+                                             int p, int h, const char* links, const void* in, int part) {
+  using T = typename Traits<P>::real;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) acc.s[a][i] = mk((T)0, (T)0);
+  if (SPLIT == 1 || part == 0 || (SPLIT == 2 && part == 0)) {
+    hop<P, R, 0, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 0, false>(acc, g, s, p, h, links, in);
+  }
+  if (SPLIT == 1 || (SPLIT == 2 && part == 1) || (SPLIT == 4 && part == 1)) {
+    hop<P, R, 1, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 1, false>(acc, g, s, p, h, links, in);
+  }
+  if (SPLIT == 1 || (SPLIT == 2 && part == 0) || (SPLIT == 4 && part == 2)) {
+    hop<P, R, 2, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 2, false>(acc, g, s, p, h, links, in);
+  }
+  if (SPLIT == 1 || (SPLIT == 2 && part == 1) || (SPLIT == 4 && part == 3)) {
+    hop<P, R, 3, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 3, false>(acc, g, s, p, h, links, in);
+  }
+}
+
+template <int P, int R, int MODE, bool REDUCE, int SPLIT>
+__global__ void __launch_bounds__(Q_THREADS) q_kernel(const Geom g, const QLaunch A) {
+  using T = typename Traits<P>::real;
+  if (A.cgs && (A.cgs[CG_DONE] != 0.0 || A.cgs[CG_PENDING] != 0.0)) return;
+  constexpr int SITES = Q_THREADS / SPLIT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int part = SPLIT == 1 ? 0 : warp % SPLIT;
+  const int jloc = (warp / SPLIT) * 32 + lane;
+  const int i = blockIdx.x * SITES + jloc;
+  const bool act = i < A.nsites;
+  int p = 0, h = 0;
+  if (A.nsites == 2 * g.Vh) {
+    // both parities: neighbouring threads take the even and odd site of the same h, so a
+    // link or spinor used by both parities is read from DRAM once while it is still in L2
+    p = i & 1;
+    h = i >> 1;
+  } else {
+    p = A.parity0;
+    h = i;
+  }
+  Spinor<T> acc;
+  if (act) {
+    const Site s = site_of(g, p, h);
+    hopping_part<P, R, SPLIT>(acc, g, s, p, h, static_cast<const char*>(A.links), A.in, part);
+  }
+  if constexpr (SPLIT > 1) {
+    extern __shared__ __align__(16) unsigned char qsm_raw[];
+    T* sm = reinterpret_cast<T*>(qsm_raw);  // [SPLIT][24][SITES]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        sm[(part * 24 + 2 * (3 * a + c)) * SITES + jloc] = act ? acc.s[a][c].re : (T)0;
+        sm[(part * 24 + 2 * (3 * a + c) + 1) * SITES + jloc] = act ? acc.s[a][c].im : (T)0;
+      }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T re = 0, im = 0;
+#pragma unroll
+        for (int k = 0; k < SPLIT; ++k) {
+          re += sm[(k * 24 + 2 * (3 * a + c)) * SITES + jloc];
+          im += sm[(k * 24 + 2 * (3 * a + c) + 1) * SITES + jloc];
+        }
+        acc.s[a][c] = mk(re, im);
+      }
+  }
+  double red[2] = {0.0, 0.0};
+  const T diag = (T)A.diag, ca = (T)A.a, cb = (T)A.b;
+  const bool read_diag = REDUCE || A.diag != 0.0;
+  Spinor<T> d, y, z;
+  if (act) {
+    if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
+    if (MODE == Q_CGUPDATE || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
+    if (MODE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
+  }
+  // out is updated in place in the CG mode: every part must have read its copy of z before
+  // any part of the block stores (each site's chunks are written by different warps)
+  if constexpr (SPLIT > 1 && MODE == Q_CGUPDATE) __syncthreads();
+  if (act) {
+    Spinor<T> res;
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        cx<T> v = (T)(-0.5) * acc.s[a][c];
+        if (read_diag) v = v + diag * d.s[a][c];
+        v = (a < 2 ? ca : -ca) * v;  // gamma5 = diag(1, 1, -1, -1)
+        res.s[a][c] = v;
+      }
+    if (MODE == Q_PLAIN) {
+      if (A.y) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c];
+      }
+    } else {
+      const double alpha = A.cgs[CG_RR] / (A.a * A.cgs[CG_TT] + A.b * A.cgs[CG_PP]);
+      const T al = (T)alpha;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res.s[a][c] = z.s[a][c] - al * (res.s[a][c] + cb * y.s[a][c]);
+    }
+    SpinorIO<P>::store(res, A.out, g.Vh, p, h, part, SPLIT);
+    if (REDUCE) {
+      T s0 = 0, s1 = 0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (SpinorIO<P>::owns(a, c, part, SPLIT)) {
+            s0 += norm2(res.s[a][c]);
+            s1 += norm2(d.s[a][c]);
+          }
+      red[0] = (double)s0;
+      red[1] = (double)s1;
+    }
+  }
+  if (REDUCE) grid_sum<2>(red, A.slot);
+}
+
+template <int P, int R, int MODE, bool REDUCE, int SPLIT>
+static cudaError_t launch_q5(const Geom& g, const QLaunch& L, cudaStream_t st) {
+  constexpr int SITES = Q_THREADS / SPLIT;
+  const int blocks = (L.nsites + SITES - 1) / SITES;
+  const size_t smem = SPLIT > 1 ? (size_t)SPLIT * 24 * SITES * sizeof(typename Traits<P>::real) : 0;
+  static bool attr = false;
+  if (smem > 48 * 1024 && !attr) {
+    cudaFuncSetAttribute(q_kernel<P, R, MODE, REDUCE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  q_kernel<P, R, MODE, REDUCE, SPLIT><<<blocks, Q_THREADS, smem, st>>>(g, L);
+  return cudaGetLastError();
+}
+
+template <int P, int R, int MODE, bool REDUCE>
+static cudaError_t launch_q4(const Geom& g, const QLaunch& L, cudaStream_t st) {
+  switch (L.split) {
+    case 1: return launch_q5<P, R, MODE, REDUCE, 1>(g, L, st);
+    case 2: return launch_q5<P, R, MODE, REDUCE, 2>(g, L, st);
+    case 4: return launch_q5<P, R, MODE, REDUCE, 4>(g, L, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int P, int R>
+static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
+  if (L.mode == Q_PLAIN)
+    return L.reduce ? launch_q4<P, R, Q_PLAIN, true>(g, L, st) : launch_q4<P, R, Q_PLAIN, false>(g, L, st);
+  return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
+}
+
+template <int P>
+static cudaError_t launch_q1(const Geom& g, const QLaunch& L, cudaStream_t st) {
+  switch (L.recon) {
+    case 18: return launch_q2<P, 18>(g, L, st);
+    case 12: return launch_q2<P, 12>(g, L, st);
+    case 8: return launch_q2<P, 8>(g, L, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace nd

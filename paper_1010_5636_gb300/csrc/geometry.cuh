@@ -1,0 +1,60 @@
+// Site geometry on the device: even-odd index <-> coordinates and neighbours, computed
+// arithmetically (no neighbour tables are read by the operator kernels).
+//
+//   lex(x) = x3 + L3*(x2 + L2*(x1 + L1*x0)),  p(x) = (x0+x1+x2+x3) mod 2,
+//   eo(x)  = p(x)*Vh + floor(lex/2),  Vh = V/2, all extents even.
+// For a site (p, h): q = floor(2h / L3) fixes (x0, x1, x2); since L3 is even, the parity of
+// x3 equals lex mod 2 = b with b = (p + x0 + x1 + x2) mod 2, so x3 = (2h mod L3) + b and
+// lex = 2h + b.  A neighbour x +- mu differs in lex by +-stride_mu (or wraps by
+// -+(L_mu - 1)*stride_mu) and has the other parity; its half index is floor(lex'/2).
+#pragma once
+#include <stdint.h>
+
+namespace nd {
+
+struct Geom {
+  int L[4];        // extents T, L1, L2, L3
+  int stride[4];   // lex strides: L1*L2*L3, L2*L3, L3, 1
+  int Vh;          // sites per parity
+  int apbc;        // 1: antiperiodic in time
+};
+
+struct Site {
+  int x[4];
+  int lex;
+};
+
+__device__ __forceinline__ Site site_of(const Geom& g, int p, int h) {
+  Site s;
+  unsigned twoh = 2u * (unsigned)h;
+  unsigned q = twoh / (unsigned)g.L[3];
+  unsigned r3 = twoh - q * (unsigned)g.L[3];
+  unsigned q2 = q / (unsigned)g.L[2];
+  s.x[2] = (int)(q - q2 * (unsigned)g.L[2]);
+  unsigned q1 = q2 / (unsigned)g.L[1];
+  s.x[1] = (int)(q2 - q1 * (unsigned)g.L[1]);
+  s.x[0] = (int)q1;
+  int b = (p + s.x[0] + s.x[1] + s.x[2]) & 1;
+  s.x[3] = (int)r3 + b;
+  s.lex = (int)twoh + b;
+  return s;
+}
+
+// Half index of the neighbour x + mu (fwd) or x - mu (bwd); *crossed = 1 if the hop wraps
+// around the time boundary (for antiperiodic boundary conditions).
+template <int MU, bool FWD>
+__device__ __forceinline__ int neighbour_h(const Geom& g, const Site& s, bool* crossed) {
+  int lex;
+  if (FWD) {
+    bool wrap = s.x[MU] == g.L[MU] - 1;
+    lex = wrap ? s.lex - (g.L[MU] - 1) * g.stride[MU] : s.lex + g.stride[MU];
+    *crossed = wrap && MU == 0;
+  } else {
+    bool wrap = s.x[MU] == 0;
+    lex = wrap ? s.lex + (g.L[MU] - 1) * g.stride[MU] : s.lex - g.stride[MU];
+    *crossed = wrap && MU == 0;
+  }
+  return lex >> 1;
+}
+
+}  // namespace nd

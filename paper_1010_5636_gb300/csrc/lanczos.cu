@@ -1,0 +1,388 @@
+// Low modes of Q (Sec. 2.3): the paper finds the lowest modes of Q^2 by minimising the Ritz
+// functional; here a thick-restart Lanczos on Q^2 in FP64 with full reorthogonalisation plays
+// that role, followed by the Rayleigh-Ritz step of Q on the found space V:
+//   u_k in V with P Q u_k = nu_k u_k,  rho_k = ||(Q - nu_k) u_k||,
+//   kappa_+-^2 = sum_{+-nu_k > 0} rho_k^2 / d_k^2.
+// d_k (distance of nu_k from the exact spectrum on the complement of the exact projector of
+// its sign; the paper gives no estimator) is estimated as
+//   d_k = min(|nu_k| + m_opp, sqrt(lambda_{l+1}) - |nu_k|),
+// m_opp = smallest |nu_j| of the opposite sign in V (sqrt(lambda_{l+1}) if there is none).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+
+#include "solver.h"
+
+namespace nd {
+
+namespace {
+
+// w = Q^2 v in FP64 (two launches through the scratch field t)
+nd_status apply_q2(nd_ctx* c, void* w, const void* v) {
+  void* t = field(c, "lz_t", 0);
+  if (!t) return fail(c, ND_ERR_OOM, "Q^2: workspace");
+  ND_TRY(q_apply(c, 0, t, v));
+  ND_TRY(q_apply(c, 0, w, t));
+  return ND_OK;
+}
+
+nd_status norm2_64(nd_ctx* c, const void* v, double* out) {
+  void* junk = field(c, "lz_junk", 0);
+  ND_TRY_CUDA(c, blas_dot(c->g, 0, v, v, slot(c, c->red_scratch), c->stream));
+  double h[3];
+  ND_TRY(read_back(c, c->red_scratch, h, 3));
+  (void)junk;
+  *out = h[2];
+  return ND_OK;
+}
+
+// h[0..2K) = (v_k, w) for the K vectors at base
+nd_status dots(nd_ctx* c, const char* base, size_t stride, int K, const void* w, std::vector<double>& h) {
+  double* dev = static_cast<double*>(workspace(c, "lz_dots", sizeof(double) * 2 * 128));
+  if (!dev) return fail(c, ND_ERR_OOM, "dots: workspace");
+  h.assign(2 * K, 0.0);
+  for (int k0 = 0; k0 < K; k0 += 64) {
+    const int kk = std::min(64, K - k0);
+    ND_TRY_CUDA(c, blas_multidot(c->g, base + k0 * stride, stride, kk, w, slot(c, dev), c->stream));
+    ND_TRY(read_back(c, dev, h.data() + 2 * k0, 2 * kk));
+  }
+  return ND_OK;
+}
+
+// out = beta * y + sum_k coef_k v_k (coef host, complex)
+nd_status lincomb(nd_ctx* c, void* out, double beta, const void* y, const char* base, size_t stride, int K,
+                  const std::vector<double>& coef) {
+  double* dev = static_cast<double*>(workspace(c, "lz_coef", sizeof(double) * 2 * 256));
+  if (!dev) return fail(c, ND_ERR_OOM, "lincomb: workspace");
+  for (int k0 = 0; k0 < K; k0 += 256) {
+    const int kk = std::min(256, K - k0);
+    ND_TRY_CUDA(c, cudaMemcpyAsync(dev, coef.data() + 2 * k0, sizeof(double) * 2 * kk, cudaMemcpyHostToDevice,
+                                   c->stream));
+    ND_TRY_CUDA(c, blas_lincomb(c->g, out, k0 == 0 ? beta : 1.0, k0 == 0 ? y : out, base + k0 * stride, stride, kk,
+                                dev, c->stream));
+    // the coefficient buffer is reused: wait before the next upload
+    ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return ND_OK;
+}
+
+}  // namespace
+
+// Plain Lanczos on Q^2 for the largest eigenvalue (iters steps, full reorthogonalisation).
+nd_status lambda_max_estimate(nd_ctx* c, int iters, double* lam) {
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  iters = std::max(2, std::min(iters, 100));
+  char* V = static_cast<char*>(field(c, "lm_V", 0, iters + 1));
+  if (!V) return fail(c, ND_ERR_OOM, "lambda_max: workspace");
+  ND_TRY_CUDA(c, blas_random(c->g, V, 12345, c->stream));
+  double n2;
+  ND_TRY(norm2_64(c, V, &n2));
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, V, 1.0 / std::sqrt(n2), V, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+  std::vector<double> T(2 * iters * iters, 0.0);
+  int m = iters;
+  for (int j = 0; j < iters; ++j) {
+    void* w = V + (j + 1) * fs;
+    ND_TRY(apply_q2(c, w, V + j * fs));
+    std::vector<double> h, h2;
+    ND_TRY(dots(c, V, fs, j + 1, w, h));
+    std::vector<double> neg(2 * (j + 1));
+    for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h[i];
+    ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
+    ND_TRY(dots(c, V, fs, j + 1, w, h2));
+    for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h2[i];
+    ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
+    for (int i = 0; i <= j; ++i) {
+      T[2 * (i * iters + j)] = h[2 * i] + h2[2 * i];
+      T[2 * (i * iters + j) + 1] = h[2 * i + 1] + h2[2 * i + 1];
+      T[2 * (j * iters + i)] = T[2 * (i * iters + j)];
+      T[2 * (j * iters + i) + 1] = -T[2 * (i * iters + j) + 1];
+    }
+    double b2;
+    ND_TRY(norm2_64(c, w, &b2));
+    if (b2 <= 1e-28 * std::max(1.0, std::fabs(T[2 * (j * iters + j)]))) {
+      m = j + 1;
+      break;
+    }
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, w, 1.0 / std::sqrt(b2), w, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+  }
+  std::vector<double> Tm(2 * m * m), ev, evec;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      Tm[2 * (i * m + j)] = T[2 * (i * iters + j)];
+      Tm[2 * (i * m + j) + 1] = T[2 * (i * iters + j) + 1];
+    }
+  hermitian_eig(m, Tm, ev, evec);
+  *lam = ev[m - 1];
+  return ND_OK;
+}
+
+// Rayleigh-Ritz of Q on the l FP64 fields at U (overwritten by the rotated u_k, ordered by
+// |nu| ascending); fills nu, rho.
+nd_status ritz_of_Q(nd_ctx* c, char* U, int l, std::vector<double>& nu, std::vector<double>& rho) {
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  char* QU = static_cast<char*>(field(c, "rr_QU", 0, l));
+  char* U2 = static_cast<char*>(field(c, "rr_U2", 0, 2 * l));
+  if (!QU || !U2) return fail(c, ND_ERR_OOM, "Rayleigh-Ritz: workspace");
+  for (int j = 0; j < l; ++j) ND_TRY(q_apply(c, 0, QU + j * fs, U + j * fs));
+  std::vector<double> M(2 * l * l), h;
+  for (int j = 0; j < l; ++j) {
+    ND_TRY(dots(c, U, fs, l, QU + j * fs, h));
+    for (int i = 0; i < l; ++i) {
+      M[2 * (i * l + j)] = h[2 * i];
+      M[2 * (i * l + j) + 1] = h[2 * i + 1];
+    }
+  }
+  // symmetrise (M is hermitian up to rounding)
+  for (int i = 0; i < l; ++i)
+    for (int j = i; j < l; ++j) {
+      const double re = 0.5 * (M[2 * (i * l + j)] + M[2 * (j * l + i)]);
+      const double im = 0.5 * (M[2 * (i * l + j) + 1] - M[2 * (j * l + i) + 1]);
+      M[2 * (i * l + j)] = re;
+      M[2 * (i * l + j) + 1] = im;
+      M[2 * (j * l + i)] = re;
+      M[2 * (j * l + i) + 1] = -im;
+    }
+  std::vector<double> ev, W;
+  hermitian_eig(l, M, ev, W);
+  std::vector<int> order(l);
+  for (int k = 0; k < l; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return std::fabs(ev[a]) < std::fabs(ev[b]); });
+  nu.assign(l, 0.0);
+  rho.assign(l, 0.0);
+  double* res = c->red_scratch + 16;
+  for (int k = 0; k < l; ++k) {
+    const int kk = order[k];
+    nu[k] = ev[kk];
+    std::vector<double> coef(2 * l);
+    for (int j = 0; j < l; ++j) {
+      coef[2 * j] = W[2 * (j * l + kk)];
+      coef[2 * j + 1] = W[2 * (j * l + kk) + 1];
+    }
+    ND_TRY(lincomb(c, U2 + k * fs, 0.0, nullptr, U, fs, l, coef));
+    ND_TRY(lincomb(c, U2 + (l + k) * fs, 0.0, nullptr, QU, fs, l, coef));
+    // rho_k = ||Q u_k - nu_k u_k||
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, U2 + (l + k) * fs, 1.0, U2 + (l + k) * fs, -nu[k], U2 + k * fs, true,
+                              slot(c, res), c->stream));
+    double r2;
+    ND_TRY(read_back(c, res, &r2, 1));
+    rho[k] = std::sqrt(std::max(0.0, r2));
+  }
+  ND_TRY_CUDA(c, cudaMemcpyAsync(U, U2, fs * l, cudaMemcpyDeviceToDevice, c->stream));
+  return ND_OK;
+}
+
+void kappas(const std::vector<double>& nu, const std::vector<double>& rho, double lam_next, double* kp, double* km) {
+  const double top = std::sqrt(std::max(0.0, lam_next));
+  double sp = 0.0, sm = 0.0;
+  const int l = (int)nu.size();
+  for (int k = 0; k < l; ++k) {
+    double m_opp = top;
+    for (int j = 0; j < l; ++j)
+      if ((nu[j] > 0) != (nu[k] > 0)) m_opp = std::min(m_opp, std::fabs(nu[j]));
+    const double d = std::min(std::fabs(nu[k]) + m_opp, top - std::fabs(nu[k]));
+    const double q = d > 0 ? rho[k] / d : INFINITY;
+    if (nu[k] > 0)
+      sp += q * q;
+    else
+      sm += q * q;
+  }
+  *kp = std::sqrt(sp);
+  *km = std::sqrt(sm);
+}
+
+// Store l modes (FP64 internal fields at src) in the context.
+nd_status store_modes(nd_ctx* c, const void* src, int l) {
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  if ((size_t)l * fs > c->evecs_cap) {
+    if (c->evecs) cudaFree(c->evecs);
+    c->evecs = nullptr;
+    c->evecs_cap = 0;
+    if (cudaMalloc(&c->evecs, (size_t)l * fs) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(c, ND_ERR_OOM, "low modes: cudaMalloc");
+    }
+    c->evecs_cap = (size_t)l * fs;
+  }
+  if (l) ND_TRY_CUDA(c, cudaMemcpyAsync(c->evecs, src, (size_t)l * fs, cudaMemcpyDeviceToDevice, c->stream));
+  c->nlow = l;
+  return ND_OK;
+}
+
+}  // namespace nd
+
+using namespace nd;
+
+extern "C" nd_status nd_lambda_max(nd_ctx* c, int iters, double* lam) {
+  if (!c || !lam) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (!c->links[0]) return fail(c, ND_ERR_STATE, "nd_lambda_max: FP64 links not set");
+  ND_TRY(lambda_max_estimate(c, iters, lam));
+  c->lam_max = *lam;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double* nu_out, double* rho_out,
+                                 double* evq2_out, nd_lowmode_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (l < 1 || l > 64 || !(tol > 0) || maxit < 1) return fail(c, ND_ERR_INVALID_ARG, "nd_lowmodes: 1 <= l <= 64");
+  if (!c->links[0]) return fail(c, ND_ERR_STATE, "nd_lowmodes: FP64 links not set");
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  double lam_max;
+  ND_TRY(lambda_max_estimate(c, 40, &lam_max));
+  c->lam_max = lam_max;
+  const int nwant = l + 1;
+  const int m = std::min(std::max(2 * nwant + 8, nwant + 20), 128);
+  const int keep = std::min(nwant + std::max(4, nwant / 2), m - 4);
+  char* V = static_cast<char*>(field(c, "lz_V", 0, m + 1));
+  char* W = static_cast<char*>(field(c, "lz_W", 0, m + 1));
+  if (!V || !W) return fail(c, ND_ERR_OOM, "nd_lowmodes: workspace");
+  ND_TRY_CUDA(c, blas_random(c->g, V, 777, c->stream));
+  double n2;
+  ND_TRY(norm2_64(c, V, &n2));
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, V, 1.0 / std::sqrt(n2), V, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+  std::vector<double> T(2 * m * m, 0.0);
+  int k = 0, apps = 0;
+  std::vector<double> theta, Y;
+  double beta_m = 0.0;
+  bool converged = false;
+  for (;;) {
+    for (int j = k; j < m; ++j) {
+      void* w = V + (j + 1) * fs;
+      ND_TRY(apply_q2(c, w, V + j * fs));
+      ++apps;
+      std::vector<double> h, h2;
+      ND_TRY(dots(c, V, fs, j + 1, w, h));
+      std::vector<double> neg(2 * (j + 1));
+      for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h[i];
+      ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
+      ND_TRY(dots(c, V, fs, j + 1, w, h2));
+      for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h2[i];
+      ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
+      for (int i = 0; i <= j; ++i) {
+        const double re = h[2 * i] + h2[2 * i], im = h[2 * i + 1] + h2[2 * i + 1];
+        if (i < k && j == k) {
+          // coupling of the kept Ritz vectors to the continuation vector
+          T[2 * (i * m + j)] = re;
+          T[2 * (i * m + j) + 1] = im;
+        } else if (i >= k || j > k) {
+          T[2 * (i * m + j)] = re;
+          T[2 * (i * m + j) + 1] = im;
+        }
+        T[2 * (j * m + i)] = T[2 * (i * m + j)];
+        T[2 * (j * m + i) + 1] = -T[2 * (i * m + j) + 1];
+      }
+      T[2 * (j * m + j) + 1] = 0.0;
+      double b2;
+      ND_TRY(norm2_64(c, w, &b2));
+      beta_m = std::sqrt(b2);
+      if (!(beta_m > 0) || !std::isfinite(beta_m)) return fail(c, ND_ERR_BREAKDOWN, "nd_lowmodes: Lanczos breakdown");
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, w, 1.0 / beta_m, w, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+    }
+    std::vector<double> Tm = T;
+    hermitian_eig(m, Tm, theta, Y);
+    lam_max = std::max(lam_max, theta[m - 1]);
+    int nconv = 0;
+    for (int i = 0; i < nwant; ++i) {
+      const double res = beta_m * std::hypot(Y[2 * ((m - 1) * m + i)], Y[2 * ((m - 1) * m + i) + 1]);
+      if (res <= tol * lam_max) ++nconv;
+    }
+    converged = nconv == nwant;
+    const int kk = converged ? nwant : keep;
+    // Ritz vectors u_i = V Y[:, i] into W, then the continuation vector v_m
+    for (int i = 0; i < kk; ++i) {
+      std::vector<double> coef(2 * m);
+      for (int j = 0; j < m; ++j) {
+        coef[2 * j] = Y[2 * (j * m + i)];
+        coef[2 * j + 1] = Y[2 * (j * m + i) + 1];
+      }
+      ND_TRY(lincomb(c, W + i * fs, 0.0, nullptr, V, fs, m, coef));
+    }
+    if (converged || apps >= maxit) break;
+    ND_TRY_CUDA(c, cudaMemcpyAsync(W + kk * fs, V + m * fs, fs, cudaMemcpyDeviceToDevice, c->stream));
+    std::swap(V, W);
+    std::swap(c->ws["lz_V"], c->ws["lz_W"]);
+    std::fill(T.begin(), T.end(), 0.0);
+    for (int i = 0; i < kk; ++i) T[2 * (i * m + i)] = theta[i];
+    k = kk;
+  }
+  if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes: Lanczos did not converge within maxit");
+  // W holds the l+1 lowest Ritz vectors of Q^2; V = span of the first l
+  c->lam_next = theta[l];
+  std::vector<double> nu, rho;
+  ND_TRY(ritz_of_Q(c, W, l, nu, rho));
+  ND_TRY(store_modes(c, W, l));
+  c->nu = nu;
+  c->rho = rho;
+  double kp, km;
+  kappas(nu, rho, c->lam_next, &kp, &km);
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
+  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
+  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
+  if (info) {
+    info->l = l;
+    info->iters = apps;
+    info->lambda_max = lam_max;
+    info->lambda_next = c->lam_next;
+    info->kappa_plus = kp;
+    info->kappa_minus = km;
+    info->max_rho = *std::max_element(rho.begin(), rho.end());
+    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  c->lam_max = lam_max;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_set_lowmodes(nd_ctx* c, int l, const double* evecs, const double* nu, double lambda_next,
+                                     nd_lowmode_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (l < 0 || l > 64 || (l > 0 && (!evecs || !nu)) || !(lambda_next > 0))
+    return fail(c, ND_ERR_INVALID_ARG, "nd_set_lowmodes: bad argument");
+  if (!c->links[0]) return fail(c, ND_ERR_STATE, "nd_set_lowmodes: FP64 links not set");
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  char* U = static_cast<char*>(field(c, "sl_U", 0, std::max(l, 1)));
+  void* t = field(c, "sl_t", 0);
+  if (!U || !t) return fail(c, ND_ERR_OOM, "nd_set_lowmodes: workspace");
+  std::vector<double> nuv(nu, nu + l), rho(l, 0.0);
+  double* res = c->red_scratch + 16;
+  for (int k = 0; k < l; ++k) {
+    ND_TRY(nd_pack_spinor(c, U + k * fs, evecs + (size_t)k * 24 * c->V, ND_FP64, 1));
+    ND_TRY(q_apply(c, 0, t, U + k * fs));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, t, 1.0, t, -nuv[k], U + k * fs, true, slot(c, res), c->stream));
+    double r2;
+    ND_TRY(read_back(c, res, &r2, 1));
+    rho[k] = std::sqrt(std::max(0.0, r2));
+  }
+  ND_TRY(store_modes(c, U, l));
+  c->nu = nuv;
+  c->rho = rho;
+  c->lam_next = lambda_next;
+  if (info) {
+    double kp = 0, km = 0;
+    kappas(nuv, rho, lambda_next, &kp, &km);
+    info->l = l;
+    info->lambda_next = lambda_next;
+    info->lambda_max = c->lam_max;
+    info->kappa_plus = kp;
+    info->kappa_minus = km;
+    info->max_rho = l ? *std::max_element(rho.begin(), rho.end()) : 0.0;
+  }
+  return ND_OK;
+}
+
+extern "C" nd_status nd_get_lowmodes(nd_ctx* c, double* evecs, double* nu) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  for (int k = 0; k < c->nlow; ++k) {
+    if (evecs)
+      ND_TRY(nd_unpack_spinor(c, evecs + (size_t)k * 24 * c->V, static_cast<char*>(c->evecs) + k * fs, ND_FP64, 1));
+    if (nu) nu[k] = c->nu[k];
+  }
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return ND_OK;
+}

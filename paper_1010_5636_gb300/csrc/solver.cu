@@ -1,0 +1,324 @@
+// Host control of the Krylov solvers: the multi-shift CG driver (device-resident scalars, a
+// status read-back every few iterations), FP64 residuals, the mixed-precision defect
+// correction, a Hermitian Jacobi eigensolver for the small projected problems, and nd_solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <numeric>
+
+#include "solver.h"
+
+namespace nd {
+
+nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a, double b, const void* y, double* result,
+                  const double* cgs) {
+  if (!c->links[prec]) return fail(c, ND_ERR_STATE, "links are not set in the precision this call needs");
+  QLaunch L{};
+  L.prec = prec;
+  L.recon = c->recon[prec];
+  L.mode = Q_PLAIN;
+  L.reduce = result != nullptr;
+  L.links = c->links[prec];
+  L.in = in;
+  L.out = out;
+  L.y = y;
+  L.diag = 4.0 + c->m;
+  L.a = a;
+  L.b = b;
+  L.parity0 = 0;
+  L.nsites = (int)c->V;
+  if (result) L.slot = slot(c, result);
+  L.cgs = cgs;
+  ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
+  return ND_OK;
+}
+
+void* field(nd_ctx* c, const char* name, int prec, int count) {
+  return workspace(c, name, (size_t)spinor_bytes(prec, c->Vh) * (size_t)count);
+}
+
+nd_status read_back(nd_ctx* c, const double* dev, double* host, int n) {
+  for (int k0 = 0; k0 < n; k0 += ND_PINNED_DOUBLES) {
+    const int k = std::min(ND_PINNED_DOUBLES, n - k0);
+    ND_TRY_CUDA(c, cudaMemcpyAsync(c->host_pinned, dev + k0, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
+    ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    std::copy(c->host_pinned, c->host_pinned + k, host + k0);
+  }
+  return ND_OK;
+}
+
+nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x_or_y, const std::vector<double>& sigma,
+                   const std::vector<double>& tol, const std::vector<double>& w, double ascale, int maxit,
+                   MsResult* out) {
+  const int n = (int)sigma.size();
+  if (n < 1 || n > CG_NMAX) return fail(c, ND_ERR_INVALID_ARG, "multi-shift CG: 1..32 shifts");
+  const size_t fs = (size_t)spinor_bytes(ps, c->Vh);
+  const size_t fx = (size_t)spinor_bytes(px, c->Vh);
+  void* r = field(c, "ms_r", ps);
+  void* t = field(c, "ms_t", ps);
+  char* p_all = static_cast<char*>(field(c, "ms_p", ps, n));
+  double* state = static_cast<double*>(workspace(c, "ms_state", sizeof(double) * CG_STATE_DOUBLES));
+  if (!r || !t || !p_all || !state) return fail(c, ND_ERR_OOM, "multi-shift CG: workspace");
+  // state: shifts, tolerances, weights, ascale
+  std::vector<double> h(CG_STATE_DOUBLES, 0.0);
+  for (int l = 0; l < n; ++l) {
+    h[sh(SH_SIGMA, l)] = sigma[l];
+    h[sh(SH_TOL, l)] = tol[l];
+    h[sh(SH_W, l)] = w.empty() ? 0.0 : w[l];
+  }
+  h[CG_ASCALE] = ascale;
+  ND_TRY_CUDA(c, cudaMemcpyAsync(state, h.data(), sizeof(double) * CG_STATE_DOUBLES, cudaMemcpyHostToDevice, c->stream));
+  // r = b, p_l = b, x = 0 (or y = 0), RR = ||b||^2
+  ND_TRY_CUDA(c, blas_axpby(c->g, ps, r, 1.0, b, 0.0, nullptr, true, slot(c, state + CG_RR), c->stream));
+  for (int l = 0; l < n; ++l) ND_TRY_CUDA(c, cudaMemcpyAsync(p_all + l * fs, b, fs, cudaMemcpyDeviceToDevice, c->stream));
+  ND_TRY_CUDA(c, cudaMemsetAsync(x_or_y, 0, ymode ? fx : fx * n, c->stream));
+  ND_TRY_CUDA(c, mscg_init(state, n, c->stream));
+  const double s0 = sigma[0];
+  int chunk = 8;
+  double hs[CG_NSCALAR];
+  for (;;) {
+    for (int k = 0; k < chunk; ++k) {
+      // K1: t = Q p_0, (||t||^2, ||p_0||^2) -> (TT, PP)
+      ND_TRY(q_apply(c, ps, t, p_all, 1.0, 0.0, nullptr, state + CG_TT, state));
+      // K2: r -= alpha (ascale Q t + sigma_0 p_0), ||r||^2 -> RRNEW
+      QLaunch L{};
+      L.prec = ps;
+      L.recon = c->recon[ps];
+      L.mode = Q_CGUPDATE;
+      L.reduce = true;
+      L.links = c->links[ps];
+      L.in = t;
+      L.out = r;
+      L.y = p_all;
+      L.diag = 4.0 + c->m;
+      L.a = ascale;
+      L.b = s0;
+      L.nsites = (int)c->V;
+      L.slot = slot(c, state + CG_RRNEW);
+      L.cgs = state;
+      ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
+      // K3, K4
+      ND_TRY_CUDA(c, mscg_scalar(state, n, maxit, c->stream));
+      ND_TRY_CUDA(c, mscg_update(c->g, ps, px, ymode, r, p_all, fs, ymode ? nullptr : x_or_y, fx,
+                                 ymode ? x_or_y : nullptr, state, n, c->stream));
+    }
+    ND_TRY(read_back(c, state, hs, CG_NSCALAR));
+    if (hs[CG_DONE] != 0.0 || hs[CG_PENDING] != 0.0) break;
+    chunk = std::min(chunk * 2, 64);
+  }
+  std::vector<double> res(n);
+  ND_TRY(read_back(c, state + sh(SH_RES, 0), res.data(), n));
+  if (out) {
+    out->iters = (int)hs[CG_ITER];
+    out->status = (int)hs[CG_STATUS];
+    out->res = res;
+  }
+  const int stt = (int)hs[CG_STATUS];
+  if (stt != ND_OK) {
+    const char* what = stt == ND_ERR_NOT_CONVERGED ? "multi-shift CG: iteration limit reached"
+                       : stt == ND_ERR_BREAKDOWN   ? "multi-shift CG: breakdown, (p, A p) <= 0"
+                                                   : "multi-shift CG: NaN or Inf";
+    return fail(c, (nd_status)stt, what);
+  }
+  return ND_OK;
+}
+
+nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale, double bnorm2,
+                     double* rel) {
+  void* t = field(c, "res_t", 0);
+  if (!t) return fail(c, ND_ERR_OOM, "residual: workspace");
+  double* res = c->red_scratch + 8;
+  ND_TRY(q_apply(c, 0, t, x));
+  ND_TRY(q_apply(c, 0, r, t, ascale, sigma, x));  // r = (ascale Q^2 + sigma) x
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, true, slot(c, res), c->stream));
+  double h;
+  ND_TRY(read_back(c, res, &h, 1));
+  *rel = std::sqrt(h / bnorm2);
+  return ND_OK;
+}
+
+nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, const std::vector<double>& sigma,
+                           const std::vector<double>& tol, double ascale, int maxit, MixedStats* st,
+                           nd_status (*sink)(void*, int, void*), void* sink_ctx) {
+  const int n = (int)sigma.size();
+  // Sloppy pass: the Krylov vectors in ps, the shifted solutions in FP32.
+  const double floor_s = ps == 2 ? 1e-3 : 1e-6;   // where the sloppy recurrence stops being trusted
+  const double floor_in = ps == 2 ? 1e-5 : 1e-5;  // inner reduction per refinement step (FP32 solves)
+  void* bS = field(c, "mx_bS", ps);
+  char* x32 = static_cast<char*>(field(c, "mx_x32", 1, n));
+  void* x64 = field(c, "mx_x64", 0);
+  void* r64 = field(c, "mx_r64", 0);
+  void* r32 = field(c, "mx_r32", 1);
+  void* e32 = field(c, "mx_e32", 1);
+  if (!bS || !x32 || !x64 || !r64 || !r32 || !e32) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
+  ND_TRY_CUDA(c, blas_convert(c->g, ps, bS, 0, b64, c->stream));
+  std::vector<double> tol_s(n);
+  for (int l = 0; l < n; ++l) tol_s[l] = std::max(tol[l], floor_s);
+  MsResult ms;
+  nd_status s = mscg_run(c, ps, 1, false, bS, x32, sigma, tol_s, {}, ascale, maxit, &ms);
+  if (s != ND_OK) return s;
+  st->iters = ms.iters;
+  st->sloppy_iters = ms.iters;
+  st->max_resid = 0.0;
+  const size_t f32 = (size_t)spinor_bytes(1, c->Vh);
+  for (int l = 0; l < n; ++l) {
+    ND_TRY_CUDA(c, blas_convert(c->g, 0, x64, 1, x32 + l * f32, c->stream));
+    double rel = 0.0;
+    int outer = 0;
+    for (;;) {
+      ND_TRY(residual64(c, r64, b64, x64, sigma[l], ascale, bnorm2, &rel));
+      if (rel <= tol[l]) break;
+      if (outer >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
+      ++outer;
+      // correction e: (A + sigma_l) e = r in FP32, from zero, to a relative reduction that
+      // reaches tol with a margin (or floor_in, whichever is larger)
+      ND_TRY_CUDA(c, blas_convert(c->g, 1, r32, 0, r64, c->stream));
+      const double inner = std::max(0.3 * tol[l] / rel, floor_in);
+      MsResult mi;
+      s = mscg_run(c, 1, 1, false, r32, e32, {sigma[l]}, {inner}, {}, ascale, maxit, &mi);
+      if (s != ND_OK && s != ND_ERR_NOT_CONVERGED) return s;
+      st->sloppy_iters += mi.iters;
+      ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, e32, c->stream));
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, x64, 1.0, x64, 1.0, r64, false, slot(c, nullptr), c->stream));
+    }
+    st->outer = std::max(st->outer, outer);
+    st->max_resid = std::max(st->max_resid, rel);
+    ND_TRY(sink(sink_ctx, l, x64));
+  }
+  return ND_OK;
+}
+
+// ------------------------------------------------------------------ Hermitian Jacobi
+void hermitian_eig(int n, std::vector<double>& A, std::vector<double>& evals, std::vector<double>& evecs) {
+  auto re = [&](int i, int j) -> double& { return A[2 * (i * n + j)]; };
+  auto im = [&](int i, int j) -> double& { return A[2 * (i * n + j) + 1]; };
+  std::vector<double> Vm(2 * n * n, 0.0);
+  for (int i = 0; i < n; ++i) Vm[2 * (i * n + i)] = 1.0;
+  double scale = 0.0;
+  for (int i = 0; i < n * n; ++i) scale = std::max(scale, std::hypot(A[2 * i], A[2 * i + 1]));
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += re(p, q) * re(p, q) + im(p, q) * im(p, q);
+    if (off <= 1e-34 * scale * scale * n * n || scale == 0.0) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double br = re(p, q), bi = im(p, q);
+        const double bm = std::hypot(br, bi);
+        if (bm <= 1e-300) continue;
+        // D = diag(1, e^{-i phi}) makes the (p, q) entry real and positive; then a real rotation.
+        const double cph = br / bm, sph = bi / bm;  // e^{i phi}
+        const double app = re(p, p), aqq = re(q, q);
+        const double zeta = (aqq - app) / (2.0 * bm);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        // G = D R with R = [[c, s], [-s, c]]:  G = [[c, s], [-s e^{-i phi}, c e^{-i phi}]]
+        // g_pp = c, g_pq = s, g_qp = -s e^{-i phi}, g_qq = c e^{-i phi}
+        const double gqp_r = -sn * cph, gqp_i = sn * sph;
+        const double gqq_r = cs * cph, gqq_i = -cs * sph;
+        // columns: A <- A G
+        for (int k = 0; k < n; ++k) {
+          const double akp_r = re(k, p), akp_i = im(k, p), akq_r = re(k, q), akq_i = im(k, q);
+          re(k, p) = cs * akp_r + (akq_r * gqp_r - akq_i * gqp_i);
+          im(k, p) = cs * akp_i + (akq_r * gqp_i + akq_i * gqp_r);
+          re(k, q) = sn * akp_r + (akq_r * gqq_r - akq_i * gqq_i);
+          im(k, q) = sn * akp_i + (akq_r * gqq_i + akq_i * gqq_r);
+          double* v = Vm.data();
+          const double vkp_r = v[2 * (k * n + p)], vkp_i = v[2 * (k * n + p) + 1];
+          const double vkq_r = v[2 * (k * n + q)], vkq_i = v[2 * (k * n + q) + 1];
+          v[2 * (k * n + p)] = cs * vkp_r + (vkq_r * gqp_r - vkq_i * gqp_i);
+          v[2 * (k * n + p) + 1] = cs * vkp_i + (vkq_r * gqp_i + vkq_i * gqp_r);
+          v[2 * (k * n + q)] = sn * vkp_r + (vkq_r * gqq_r - vkq_i * gqq_i);
+          v[2 * (k * n + q) + 1] = sn * vkp_i + (vkq_r * gqq_i + vkq_i * gqq_r);
+        }
+        // rows: A <- G^dagger A;  (G^dagger)_pk = conj(g_kp), rows p, q mix with conj(G) columns
+        for (int k = 0; k < n; ++k) {
+          const double apk_r = re(p, k), apk_i = im(p, k), aqk_r = re(q, k), aqk_i = im(q, k);
+          // new_p = conj(g_pp) a_p + conj(g_qp) a_q ; new_q = conj(g_pq) a_p + conj(g_qq) a_q
+          re(p, k) = cs * apk_r + (gqp_r * aqk_r + gqp_i * aqk_i);
+          im(p, k) = cs * apk_i + (gqp_r * aqk_i - gqp_i * aqk_r);
+          re(q, k) = sn * apk_r + (gqq_r * aqk_r + gqq_i * aqk_i);
+          im(q, k) = sn * apk_i + (gqq_r * aqk_i - gqq_i * aqk_r);
+        }
+        re(p, q) = im(p, q) = re(q, p) = im(q, p) = 0.0;
+        im(p, p) = im(q, q) = 0.0;
+      }
+  }
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return re(a, a) < re(b, b); });
+  evals.assign(n, 0.0);
+  evecs.assign(2 * n * n, 0.0);
+  for (int k = 0; k < n; ++k) {
+    evals[k] = re(order[k], order[k]);
+    for (int i = 0; i < n; ++i) {
+      evecs[2 * (i * n + k)] = Vm[2 * (i * n + order[k])];
+      evecs[2 * (i * n + k) + 1] = Vm[2 * (i * n + order[k]) + 1];
+    }
+  }
+}
+
+}  // namespace nd
+
+using namespace nd;
+
+extern "C" nd_status nd_solve(nd_ctx* c, double* const* x, const double* b, const double* shifts, int n, double tol,
+                              int maxit, nd_prec inner, nd_solve_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (!x || !b || !shifts || n < 1 || n > CG_NMAX || !(tol > 0) || maxit < 1 || inner < ND_FP64 || inner > ND_FP16)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_solve: bad argument (1 <= n <= 32, tol > 0, maxit >= 1)");
+  for (int k = 0; k < n; ++k)
+    if (!x[k] || !(shifts[k] >= 0.0)) return fail(c, ND_ERR_INVALID_ARG, "nd_solve: null x or negative shift");
+  if (!c->links[0] || !c->links[inner] || (inner != ND_FP64 && !c->links[1]))
+    return fail(c, ND_ERR_STATE, "nd_solve: links must be set in FP64, in the inner precision and (mixed) FP32");
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int bb) { return shifts[a] < shifts[bb]; });
+  std::vector<double> sig(n), tols(n, tol);
+  for (int l = 0; l < n; ++l) sig[l] = shifts[perm[l]];
+  void* b64 = field(c, "solve_b64", 0);
+  if (!b64) return fail(c, ND_ERR_OOM, "nd_solve: workspace");
+  ND_TRY(nd_pack_spinor(c, b64, b, ND_FP64, 1));
+  double bn2;
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, b64, 1.0, b64, 0.0, nullptr, true, slot(c, c->red_scratch), c->stream));
+  ND_TRY(read_back(c, c->red_scratch, &bn2, 1));
+  nd_solve_info inf{};
+  if (bn2 == 0.0) {
+    for (int k = 0; k < n; ++k) ND_TRY_CUDA(c, cudaMemsetAsync(x[k], 0, sizeof(double) * 24 * c->V, c->stream));
+    if (info) *info = inf;
+    return ND_OK;
+  }
+  if (!std::isfinite(bn2)) return fail(c, ND_ERR_NAN, "nd_solve: source has NaN or Inf");
+  nd_status s = ND_OK;
+  if (inner == ND_FP64) {
+    char* x64 = static_cast<char*>(field(c, "solve_x64", 0, n));
+    void* r64 = field(c, "solve_r64", 0);
+    if (!x64 || !r64) return fail(c, ND_ERR_OOM, "nd_solve: workspace");
+    MsResult ms;
+    s = mscg_run(c, 0, 0, false, b64, x64, sig, tols, {}, 1.0, maxit, &ms);
+    if (s != ND_OK && s != ND_ERR_NOT_CONVERGED) return s;
+    inf.iters = inf.sloppy_iters = ms.iters;
+    const size_t f64 = (size_t)spinor_bytes(0, c->Vh);
+    for (int l = 0; l < n; ++l) {
+      double rel;
+      ND_TRY(residual64(c, r64, b64, x64 + l * f64, sig[l], 1.0, bn2, &rel));
+      inf.max_resid = std::max(inf.max_resid, rel);
+      ND_TRY(nd_unpack_spinor(c, x[perm[l]], x64 + l * f64, ND_FP64, 1));
+    }
+  } else {
+    MixedStats ms;
+    auto sink = [&](int l, void* x64) -> nd_status { return nd_unpack_spinor(c, x[perm[l]], x64, ND_FP64, 1); };
+    s = mixed_solve(c, (int)inner, b64, bn2, sig, tols, 1.0, maxit, &ms, sink);
+    if (s != ND_OK) return s;
+    inf.iters = ms.iters;
+    inf.sloppy_iters = ms.sloppy_iters;
+    inf.outer = ms.outer;
+    inf.max_resid = ms.max_resid;
+  }
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  return s;
+}

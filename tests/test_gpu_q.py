@@ -1,0 +1,165 @@
+"""GPU parity of the site tables and of Q = gamma5 D_W (Sec. 2.1) against the oracle,
+through the C-ABI: bit-exact tables, FP64 Q <= 1e-12, FP32 Q <= 1e-5 (relative L2),
+FP16-storage Q with its measured error stated, for every link form."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import geometry, wilson
+from tests.gpu_util import dev, host, rel
+
+pytestmark = pytest.mark.gpu
+M = -1.4
+TOL = {0: 1e-12, 1: 1e-5, 2: 2e-3}
+
+
+@pytest.fixture(scope="module")
+def nd():
+    import paper_1010_5636_gb300 as nd
+    nd.lib()
+    return nd
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (4, 6, 2, 8), (6, 4, 4, 6), (16, 16, 16, 32)])
+def test_eo_tables_bit_exact(nd, dims):
+    import torch
+    ctx = nd.nd_create(dims)
+    try:
+        V = int(np.prod(dims))
+        l2e = torch.empty(V, dtype=torch.int32, device="cuda")
+        nbr = torch.empty((8, V), dtype=torch.int32, device="cuda")
+        nd.nd_eo_tables(ctx, l2e, nbr)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(l2e), geometry.lex_to_eo(dims))
+        assert np.array_equal(host(nbr), geometry.neighbour_eo(dims))
+    finally:
+        nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_pack_round_trip(nd, prec):
+    dims = (4, 6, 2, 8)
+    psi = synth.spinor(dims, seed=1)
+    ctx = nd.nd_create(dims)
+    try:
+        f = dev(psi)
+        import torch
+        buf = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+        nd.nd_pack_spinor(ctx, buf, f, prec)
+        back = torch.empty_like(f)
+        nd.nd_unpack_spinor(ctx, back, buf, prec)
+        torch.cuda.synchronize()
+        if prec == 0:
+            assert np.array_equal(host(back), psi)
+        else:
+            assert rel(host(back), psi) < (1e-7 if prec == 1 else 1e-3)
+    finally:
+        nd.nd_destroy(ctx)
+
+
+def _q_case(nd, dims, kind, prec, recon, antiperiodic=False, seed=0):
+    import torch
+    U = synth.gauge_field(dims, kind, seed=seed, eps=0.3)
+    psi = synth.spinor(dims, seed=1)
+    expect = wilson.apply_Q(U, psi, dims, M, antiperiodic)
+    ctx = nd.nd_create(dims, antiperiodic_t=antiperiodic, m=M)
+    try:
+        rc = [0, 0, 0]
+        rc[prec] = recon
+        nd.nd_set_links(ctx, dev(U), rc)
+        inb = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+        outb = torch.empty_like(inb)
+        nd.nd_pack_spinor(ctx, inb, dev(psi), prec)
+        nd.nd_apply_Q(ctx, outb, inb, prec)
+        got = torch.empty((int(np.prod(dims)), 4, 3), dtype=torch.complex128, device="cuda")
+        nd.nd_unpack_spinor(ctx, got, outb, prec)
+        torch.cuda.synchronize()
+        return rel(host(got), expect)
+    finally:
+        nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("recon", [18, 12, 8])
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 4, 6), (4, 6, 2, 8)])
+def test_Q_haar(nd, prec, recon, dims):
+    err = _q_case(nd, dims, "haar", prec, recon)
+    assert err <= TOL[prec], err
+
+
+@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 8), (2, 12)])
+def test_Q_antiperiodic(nd, prec, recon):
+    assert _q_case(nd, (4, 4, 2, 6), "haar", prec, recon, antiperiodic=True) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_Q_free_field_recon12(nd, prec):
+    assert _q_case(nd, (4, 4, 4, 4), "unit", prec, 12) <= TOL[prec]
+
+
+def test_recon8_rejects_unit_links(nd):
+    dims = (2, 2, 2, 2)
+    ctx = nd.nd_create(dims)
+    try:
+        with pytest.raises(nd.NdError) as e:
+            nd.nd_set_links(ctx, dev(synth.gauge_field(dims, "unit")), (0, 8, 0))
+        assert e.value.status == nd.ND_ERR_INVALID_ARG
+    finally:
+        nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("diag", [2.6, 0.0])
+def test_Q_parity_block(nd, parity, diag):
+    import torch
+    dims = (4, 4, 6, 4)
+    V = int(np.prod(dims))
+    U = synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)
+    psi = synth.spinor(dims, seed=2)
+    full = wilson.apply_Q(U, psi, dims, M)
+    g5psi = psi.copy()
+    g5psi[:, 2:] *= -1
+    expect = full - (4 + M - diag) * g5psi
+    par = geometry.coords(dims).sum(axis=1) % 2
+    ctx = nd.nd_create(dims, m=M)
+    try:
+        nd.nd_set_links(ctx, dev(U), (18, 12, 0))
+        for prec in (0, 1):
+            inb = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+            outb = torch.zeros_like(inb)
+            nd.nd_pack_spinor(ctx, inb, dev(psi), prec)
+            nd.nd_apply_Q_parity(ctx, outb, inb, prec, parity, diag)
+            got = torch.empty((V, 4, 3), dtype=torch.complex128, device="cuda")
+            nd.nd_unpack_spinor(ctx, got, outb, prec)
+            torch.cuda.synchronize()
+            g = host(got)[par == parity]
+            assert rel(g, expect[par == parity]) <= TOL[prec]
+    finally:
+        nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("dims", [(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)])
+def test_Q_full_size_fp32(nd, dims):
+    """The bench's lattices (near-identity links, as in the bandwidth sweep), whole-field parity."""
+    assert _q_case(nd, dims, "near_identity", 1, 12) <= TOL[1]
+    assert _q_case(nd, dims, "near_identity", 1, 8) <= TOL[1]
+
+
+def test_Q_full_size_fp64(nd):
+    assert _q_case(nd, (64, 32, 32, 32), "near_identity", 0, 18) <= TOL[0]
+
+
+def test_Q_canonical(nd):
+    import torch
+    dims = (4, 4, 4, 6)
+    U = synth.gauge_field(dims, "haar", seed=4)
+    psi = synth.spinor(dims, seed=5)
+    ctx = nd.nd_create(dims, m=M)
+    try:
+        nd.nd_set_links(ctx, dev(U), (18, 0, 0))
+        out = torch.empty_like(dev(psi))
+        nd.nd_apply_Q_canonical(ctx, out, dev(psi))
+        torch.cuda.synchronize()
+        assert rel(host(out), wilson.apply_Q(U, psi, dims, M)) <= 1e-12
+    finally:
+        nd.nd_destroy(ctx)
