@@ -1,0 +1,460 @@
+#!/usr/bin/env python3
+"""Benchmark of the Neuberger-Dirac hot path on one GB300 per rank.
+
+Headline (the Wilson-Dirac bandwidth sweep's largest lattice): the even-odd Dslash, i.e. the
+two hopping blocks of Q = gamma5 D_W (out_even <- in_odd, out_odd <- in_even, gamma5 fused) in
+FP32 with 12-real links on a 64 x 32^3 lattice of near-identity SU(3) links (eps = 0.3).
+One step = both hopping blocks over the whole lattice (2 kernel launches).
+value = algorithmic bytes of the step / step time, in GB/s; the per-site algorithmic bytes
+are (24 input + 8 * 12 link + 24 output reals) * 4 bytes = 576 B (each input spinor and link
+counted once per pass, as the kernel's minimal DRAM traffic).
+
+Also measured and reported: the bandwidth sweep (FP64/FP32/FP16 x 18/12/8 links, full Q and
+half pass) and D_N applies per second on 16^3 x 32 Haar links with 20 Zolotarev poles and 20
+FP64 Lanczos modes, rational part solved to 1e-10: pure FP64 against mixed FP32 / FP16-storage
+inner iterations with FP64 defect correction.
+
+Replicas only on N GPUs: each rank runs the same independent workload (no collective on the
+data path); value sums the ranks' bytes over the slowest rank's time.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Dslash GB/s (frac of HBM peak); D_N applies/s at 1e-10 resid, mixed vs FP64"
+DIMS = (64, 32, 32, 32)
+DN_DIMS = (32, 16, 16, 16)
+RECON = 12
+# low modes: residual ||Q^2 u - theta u|| <= 1e-6 lambda_max (FP32 Chebyshev filter, FP64
+# orthogonalisation and Ritz projection); the 20 lowest modes of the 16^3x32 Haar field lie in a
+# dense band, so their kappa_+- are reported with the result
+LOWMODE_TOL = 1e-6
+WORD = {0: 8, 1: 4, 2: 2}
+
+
+def site_bytes(prec, recon, half=True):
+    """Algorithmic bytes per output site: (in + links + out), half pass or fused full Q."""
+    nl = 8 if half else 4
+    if prec == 2:
+        return 48 * 2 + 8 + nl * recon * 2
+    return (48 + nl * recon) * WORD[prec]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while active."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+                for k, n in enumerate(names):
+                    if r[4 + k].lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        load = [s for s in sm if s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier_sync(world):
+    import torch
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_baseline(seconds_target=15.0):
+    """The oracle's Q (plain C, FP64, OpenMP over sites) on the headline lattice, a bounded
+    number of applications; the rate is expressed in the headline's GB/s-equivalent units
+    (output sites per second times the headline's algorithmic bytes per site)."""
+    import numpy as np
+
+    import synth
+    from oracle import wilson
+    cores = len(os.sched_getaffinity(0))
+    wilson.set_threads(cores)
+    U = synth.gauge_field(DIMS, "near_identity", seed=0, eps=0.3)
+    psi = synth.spinor(DIMS, seed=1)
+    V = int(np.prod(DIMS))
+    wilson.apply_Q(U, psi, DIMS, -1.4)  # warm-up
+    n, t0 = 0, time.perf_counter()
+    while True:
+        wilson.apply_Q(U, psi, DIMS, -1.4)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or n >= 50:
+            break
+    rate = n * V / el
+    return {"value": rate * site_bytes(1, RECON) / 1e9, "unit": "GB/s", "cores": wilson.get_threads(),
+            "kind": "oracle",
+            "sample": f"{n} applications of the oracle's FP64 Q (both parities) on {DIMS}, {el:.1f} s; "
+                      f"rate in output sites/s x {site_bytes(1, RECON)} B (the headline's bytes per site)",
+            "sites_per_s": rate}
+
+
+def reference_arm(args):
+    # the oracle runs on the host cores of rank 0 only; other ranks exit without work
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+    import numpy as np
+
+    import synth
+    from oracle import wilson
+    cores = len(os.sched_getaffinity(0))
+    wilson.set_threads(cores)
+    U = synth.gauge_field(DIMS, "near_identity", seed=0, eps=0.3)
+    psi = synth.spinor(DIMS, seed=1)
+    V = int(np.prod(DIMS))
+    # one step = one application of the oracle's Q to the whole lattice (well under a second on 16
+    # cores), so --steps 50 stays within a minute or two
+    for _ in range(min(warm, 1)):
+        wilson.apply_Q(U, psi, DIMS, -1.4)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        wilson.apply_Q(U, psi, DIMS, -1.4)
+    el = time.perf_counter() - t0
+    rate = steps * V / el
+    val = rate * site_bytes(1, RECON) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": 1, "steps": steps,
+            "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"even-odd Dslash on {DIMS[1]}^3x{DIMS[0]} (oracle: FP64 Q, both parities)",
+                       "lattice": list(DIMS), "links": "near-identity SU(3), eps=0.3, seed 0"},
+            "cpu_baseline": {"value": val, "unit": "GB/s", "cores": wilson.get_threads(), "kind": "oracle",
+                             "sample": f"{steps} full applications of the oracle's Q on {DIMS}"},
+            "e2e": {"value": val, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def dslash_phase(nd, torch, steps, warm, world, clocks):
+    """Headline: K steps of the even-odd Dslash (2 launches each) on 64x32^3, FP32, 12-real links."""
+    import numpy as np
+
+    import synth
+    V = int(np.prod(DIMS))
+    U = torch.from_numpy(synth.gauge_field(DIMS, "near_identity", seed=0, eps=0.3)).cuda()
+    psi_h = torch.from_numpy(synth.spinor(DIMS, seed=1))
+    ctx = nd.nd_create(DIMS, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, U, (0, RECON, 0))
+    del U
+    prec = nd.ND_FP32
+    a = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    nd.nd_pack_spinor(ctx, a, psi_h.cuda(), prec)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        nd.nd_apply_Q_parity(ctx, b, a, prec, 0, 0.0)
+        nd.nd_apply_Q_parity(ctx, b, a, prec, 1, 0.0)
+
+    for _ in range(max(3, warm)):
+        step()
+    barrier_sync(world)
+    # per-launch durations with events on the launching stream (roofline of the kernel)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2 * steps)]
+    with clocks:
+        # the sampler needs a few hundred ms to start: keep the GPU on the same kernel for ~1 s
+        # (untimed) so that samples cover the load the timed region sees
+        tl = time.perf_counter()
+        while time.perf_counter() - tl < 1.0:
+            for _ in range(200):
+                step()
+            torch.cuda.synchronize()
+        barrier_sync(world)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for k in range(steps):
+            ev[2 * k][0].record(stream)
+            nd.nd_apply_Q_parity(ctx, b, a, prec, 0, 0.0)
+            ev[2 * k][1].record(stream)
+            ev[2 * k + 1][0].record(stream)
+            nd.nd_apply_Q_parity(ctx, b, a, prec, 1, 0.0)
+            ev[2 * k + 1][1].record(stream)
+        t1.record(stream)
+        barrier_sync(world)
+    total_ms = t0.elapsed_time(t1)
+    launch_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    total_ms = max_over_ranks(total_ms, world)
+    bytes_step = V * site_bytes(prec, RECON)
+    gbs = sum_over_ranks(bytes_step * steps, world) / (total_ms * 1e-3) / 1e9
+    avg_launch = sum(launch_ms) / len(launch_ms)
+    per_launch_bytes = bytes_step / 2
+    # end to end through the public API with host buffers: pinned canonical FP64 input copied in,
+    # packed, both hopping blocks, unpacked, result copied back -- every step
+    psi_pin = psi_h.pin_memory()
+    out_pin = torch.empty_like(psi_pin).pin_memory()
+    dev_in = torch.empty_like(psi_pin, device="cuda")
+    dev_out = torch.empty_like(dev_in)
+
+    def e2e_step():
+        dev_in.copy_(psi_pin, non_blocking=True)
+        nd.nd_pack_spinor(ctx, a, dev_in, prec)
+        step()
+        nd.nd_unpack_spinor(ctx, dev_out, b, prec)
+        out_pin.copy_(dev_out, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    barrier_sync(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        e2e_step()
+    e1.record(stream)
+    barrier_sync(world)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_gbs = sum_over_ranks(bytes_step * steps, world) / (e2e_ms * 1e-3) / 1e9
+    nbytes_io = psi_pin.numel() * psi_pin.element_size()
+    nd.nd_destroy(ctx)
+    return {"total_ms": total_ms, "gbs": gbs, "avg_launch_ms": avg_launch, "per_launch_bytes": per_launch_bytes,
+            "e2e_gbs": e2e_gbs, "io_bytes": nbytes_io, "launches": 2 * steps, "V": V}
+
+
+def sweep_phase(nd, torch):
+    """Bandwidth sweep: every precision x link form, full fused Q and the one-parity pass (median of
+    10 launches with a 512 MB write between launches to flush L2)."""
+    import numpy as np
+
+    import synth
+    V = int(np.prod(DIMS))
+    U = torch.from_numpy(synth.gauge_field(DIMS, "near_identity", seed=0, eps=0.3)).cuda()
+    psi = torch.from_numpy(synth.spinor(DIMS, seed=1)).cuda()
+    ctx = nd.nd_create(DIMS, m=-1.4, s=0.4)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    out = []
+    for prec in (1, 2, 0):
+        for recon in (18, 12, 8):
+            rc = [0, 0, 0]
+            rc[prec] = recon
+            nd.nd_set_links(ctx, U, rc)
+            a = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+            b = torch.empty_like(a)
+            nd.nd_pack_spinor(ctx, a, psi, prec)
+            for half in (True, False):
+                f = (lambda: nd.nd_apply_Q_parity(ctx, b, a, prec, 0, 0.0)) if half else \
+                    (lambda: nd.nd_apply_Q(ctx, b, a, prec))
+                for _ in range(3):
+                    f()
+                ts = []
+                for _ in range(10):
+                    flush.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    f()
+                    e1.record()
+                    torch.cuda.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                t = float(np.median(ts)) * 1e-3
+                sites = V // 2 if half else V
+                gbs = sites * site_bytes(prec, recon, half) / t / 1e9
+                out.append({"prec": ["fp64", "fp32", "fp16"][prec], "recon": recon,
+                            "kernel": "half" if half else "full_Q", "us": round(t * 1e6, 1),
+                            "GB/s": round(gbs, 1), "Gsite/s": round(sites / t / 1e9, 3)})
+            del a, b
+    nd.nd_destroy(ctx)
+    return out
+
+
+def dn_phase(nd, torch, reps):
+    """D_N applies/s: 16^3x32 Haar links, 20 poles, 20 FP64 Lanczos modes, rational part to 1e-10."""
+    import numpy as np
+
+    import synth
+    U = torch.from_numpy(synth.gauge_field(DN_DIMS, "haar", seed=0)).cuda()
+    eta = torch.from_numpy(synth.spinor(DN_DIMS, seed=1)).cuda()
+    ctx = nd.nd_create(DN_DIMS, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, U, (18, 12, 12))
+    t0 = time.perf_counter()
+    nu, rho, ev, li = nd.nd_lowmodes(ctx, 20, LOWMODE_TOL, 2000000)
+    t_low = time.perf_counter() - t0
+    res = {"workload": f"D_N on {DN_DIMS[1]}^3x{DN_DIMS[0]} Haar links (seed 0), 20 poles, 20 deflated low modes "
+                       "(FP32-filtered subspace iteration, FP64 orthogonalisation and Ritz projection, "
+                       f"residual {LOWMODE_TOL} lambda_max), rational part to 1e-10 (relative)",
+           "lowmodes_s": round(t_low, 3), "lowmodes_q2_applications": li.iters,
+           "lambda_max": li.lambda_max, "lambda_next": li.lambda_next, "kappa_plus": li.kappa_plus,
+           "kappa_minus": li.kappa_minus}
+    outs = {}
+    for name, inner in (("fp64", 0), ("mixed_fp32", 1), ("mixed_fp16", 2)):
+        p = nd.dn_params(20, 0.0, 0.0, 1e-10, 200000, inner, 0.0, False)
+        o = torch.empty_like(eta)
+        info = nd.nd_apply_DN(ctx, o, eta, p)  # warm-up (allocates workspaces)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = nd.nd_apply_DN(ctx, o, eta, p)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        outs[name] = o.clone()
+        res[name] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "krylov_iters": info.iters,
+                     "sloppy_iters": info.sloppy_iters, "refinement_sweeps": info.outer,
+                     "max_shift_resid": info.max_resid, "delta_zolotarev": info.delta, "eps": info.eps}
+    base = outs["fp64"]
+    for name in ("mixed_fp32", "mixed_fp16"):
+        res[name]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs[name] - base) /
+                                              torch.linalg.vector_norm(base))
+        res[name]["speedup_vs_fp64"] = round(res["fp64"]["s_per_apply"] / res[name]["s_per_apply"], 3)
+    nd.nd_destroy(ctx)
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-dn", action="store_true")
+    ap.add_argument("--dn-reps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+    world, rank, local = dist_setup(args)
+    import torch
+
+    import paper_1010_5636_gb300 as nd
+    torch.cuda.set_device(local)
+    nd.lib(build_if_missing=False)
+    steps, warm = max(1, args.steps), max(3, args.warmup)
+    clocks = ClockSampler(local)
+    d = dslash_phase(nd, torch, steps, warm, world, clocks)
+    peaks, src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = d["per_launch_bytes"] / (d["avg_launch_ms"] * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            traffic = tj.get("dram_bytes_per_launch_scaled")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": round(d["gbs"], 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": round(d["total_ms"] / steps, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"even-odd Dslash (both hopping blocks of Q, gamma5 fused) on {DIMS[1]}^3x{DIMS[0]}, "
+                               f"FP32 storage, {RECON}-real links, near-identity SU(3) links eps=0.3",
+                   "lattice": list(DIMS), "recon": RECON, "bytes_per_site": site_bytes(1, RECON),
+                   "l2": "inputs larger than L2: spinor 201 MB + links 403 MB vs 129 MB L2, no flush",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 4), "peak_source": f"hbm_gbs of {src}", "traffic": traffic},
+        "frac_of_nominal_8TBs": round(d["gbs"] / world / 8000.0, 4),
+        "e2e": {"value": round(d["e2e_gbs"], 1), "unit": "GB/s", "h2d_bytes_per_step": d["io_bytes"],
+                "d2h_bytes_per_step": d["io_bytes"]},
+        "gpu_launches": d["launches"],
+        "clocks": clocks.summary(),
+    }
+    if not args.no_sweep:
+        line["sweep"] = sweep_phase(nd, torch)
+    if not args.no_dn:
+        line["dn"] = dn_phase(nd, torch, args.dn_reps)
+    if rank == 0 and world == 1:
+        line["cpu_baseline"] = oracle_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -96,15 +96,17 @@ __global__ void __launch_bounds__(Q_THREADS) q_kernel(const Geom g, const QLaunc
   double red[2] = {0.0, 0.0};
   const T diag = (T)A.diag, ca = (T)A.a, cb = (T)A.b;
   const bool read_diag = REDUCE || A.diag != 0.0;
+  constexpr bool IN_PLACE = MODE == Q_CGUPDATE || MODE == Q_XPAY2;
   Spinor<T> d, y, z;
   if (act) {
     if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
-    if (MODE == Q_CGUPDATE || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
+    if (MODE != Q_PLAIN || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
     if (MODE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
+    if (MODE == Q_XPAY2) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
   }
-  // out is updated in place in the CG mode: every part must have read its copy of z before
-  // any part of the block stores (each site's chunks are written by different warps)
-  if constexpr (SPLIT > 1 && MODE == Q_CGUPDATE) __syncthreads();
+  // in the in-place modes every part must have read its copy of z before any part of the
+  // block stores (each site's chunks are written by different warps)
+  if constexpr (SPLIT > 1 && IN_PLACE) __syncthreads();
   if (act) {
     Spinor<T> res;
 #pragma unroll
@@ -123,6 +125,12 @@ __global__ void __launch_bounds__(Q_THREADS) q_kernel(const Geom g, const QLaunc
 #pragma unroll
           for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c];
       }
+    } else if (MODE == Q_XPAY2) {
+      const T cc = (T)A.c;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c] + cc * z.s[a][c];
     } else {
       const double alpha = A.cgs[CG_RR] / (A.a * A.cgs[CG_TT] + A.b * A.cgs[CG_PP]);
       const T al = (T)alpha;
@@ -175,9 +183,15 @@ static cudaError_t launch_q4(const Geom& g, const QLaunch& L, cudaStream_t st) {
 
 template <int P, int R>
 static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
-  if (L.mode == Q_PLAIN)
-    return L.reduce ? launch_q4<P, R, Q_PLAIN, true>(g, L, st) : launch_q4<P, R, Q_PLAIN, false>(g, L, st);
-  return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
+  switch (L.mode) {
+    case Q_PLAIN:
+      return L.reduce ? launch_q4<P, R, Q_PLAIN, true>(g, L, st) : launch_q4<P, R, Q_PLAIN, false>(g, L, st);
+    case Q_XPAY2:
+      return L.reduce ? launch_q4<P, R, Q_XPAY2, true>(g, L, st) : launch_q4<P, R, Q_XPAY2, false>(g, L, st);
+    case Q_CGUPDATE:
+      return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 template <int P>

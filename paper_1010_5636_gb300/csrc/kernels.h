@@ -36,9 +36,10 @@ constexpr int CG_NMAX = 32;
 constexpr int CG_STATE_DOUBLES = CG_NSCALAR + SH_NARRAY * CG_NMAX;
 __host__ __device__ inline int sh(int array, int l) { return CG_NSCALAR + array * CG_NMAX + l; }
 
-enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1 };
+enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2 };
 
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y      (Q_PLAIN; y may be null)
+// out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y + c * z   (Q_XPAY2; z may alias out)
 // out = out - alpha * (a * gamma5(diag * in - 1/2 hop(in)) + b * y),
 //       alpha = cgs[CG_RR] / (a * cgs[CG_TT] + b * cgs[CG_PP])      (Q_CGUPDATE)
 // Output sites: parity `parity0` only (nsites = Vh) or both parities (nsites = 2 Vh).
@@ -52,7 +53,8 @@ struct QLaunch {
   const void* in;
   void* out;
   const void* y;
-  double diag, a, b;
+  const void* z;  // Q_XPAY2 only
+  double diag, a, b, c;
   int parity0, nsites;
   ReduceSlot slot;
   const double* cgs;  // multi-shift CG scalars, or null; kernels skip when cgs[CG_DONE] or cgs[CG_PENDING] != 0

@@ -1,6 +1,7 @@
 // Low modes of Q (Sec. 2.3): the paper finds the lowest modes of Q^2 by minimising the Ritz
-// functional; here a thick-restart Lanczos on Q^2 in FP64 with full reorthogonalisation plays
-// that role, followed by the Rayleigh-Ritz step of Q on the found space V:
+// functional; here a Chebyshev-filtered subspace iteration on Q^2 (FP32 or FP64 filter, FP64
+// orthonormalisation and Rayleigh-Ritz) plays that role, followed by the Rayleigh-Ritz step of
+// Q on the found space V:
 //   u_k in V with P Q u_k = nu_k u_k,  rho_k = ||(Q - nu_k) u_k||,
 //   kappa_+-^2 = sum_{+-nu_k > 0} rho_k^2 / d_k^2.
 // d_k (distance of nu_k from the exact spectrum on the complement of the exact projector of
@@ -11,6 +12,8 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
+#include <cstdlib>
 
 #include "solver.h"
 
@@ -222,6 +225,127 @@ extern "C" nd_status nd_lambda_max(nd_ctx* c, int iters, double* lam) {
   return ND_OK;
 }
 
+namespace nd {
+
+// Chebyshev filter x <- C_d(Q^2) x with C_d(t) = T_d(L(t)) / T_d(L(0)), L mapping [lo, hi] onto
+// [-1, 1]: modes below lo are amplified relative to the damped interval, and the normalisation
+// at t = 0 (Q^2 >= 0) keeps every value in [-1, 1], so no precision overflows.  Scaled
+// three-term recurrence with s_1 = e / (0 - c), s_{k+1} = 1 / (2 / s_1 - s_k):
+//   C_1 = (s_1 / e) (A - c),  C_{k+1} = (2 s_{k+1} / e) (A - c) C_k - s_k s_{k+1} C_{k-1},
+// e = (hi - lo) / 2, c = (hi + lo) / 2.  Evaluated in precision prec on the FP64 field x
+// (converted in and out); every step is two Q launches, the second carrying the recurrence
+// terms in its epilogue.
+nd_status cheb_filter(nd_ctx* c, int prec, void* x64, int deg, double lo, double hi) {
+  const double e = 0.5 * (hi - lo), cc = 0.5 * (hi + lo);
+  const double s1 = e / (0.0 - cc), tau = 2.0 / s1;
+  void* ya = field(c, prec == 0 ? "cf_ya64" : "cf_ya32", prec);
+  void* yb = field(c, prec == 0 ? "cf_yb64" : "cf_yb32", prec);
+  void* t = field(c, prec == 0 ? "cf_t64" : "cf_t32", prec);
+  if (!ya || !yb || !t) return fail(c, ND_ERR_OOM, "Chebyshev filter: workspace");
+  ND_TRY_CUDA(c, blas_convert(c->g, prec, ya, 0, x64, c->stream));  // C_0 x
+  ND_TRY(q_apply(c, prec, t, ya));
+  ND_TRY(q_apply(c, prec, yb, t, s1 / e, -cc * s1 / e, ya));  // C_1 x
+  void* prev = ya;
+  void* cur = yb;
+  double s = s1;
+  for (int k = 1; k < deg; ++k) {
+    const double sn = 1.0 / (tau - s);
+    ND_TRY(q_apply(c, prec, t, cur));
+    // C_{k+1} x = (2 sn / e)(Q^2 - c) C_k x - s sn C_{k-1} x, written over C_{k-1} x
+    ND_TRY(q_apply(c, prec, prev, t, 2.0 * sn / e, -2.0 * sn * cc / e, cur, nullptr, nullptr, prev, -s * sn));
+    std::swap(prev, cur);
+    s = sn;
+  }
+  ND_TRY_CUDA(c, blas_convert(c->g, 0, x64, prec, cur, c->stream));
+  return ND_OK;
+}
+
+// Classical Gram-Schmidt with one reorthogonalisation pass over the k FP64 fields at X.
+nd_status orthonormalise(nd_ctx* c, char* X, int k, size_t fs) {
+  for (int j = 0; j < k; ++j) {
+    void* x = X + j * fs;
+    for (int attempt = 0; attempt < 3; ++attempt) {
+      for (int pass = 0; pass < 2 && j > 0; ++pass) {
+        std::vector<double> h;
+        ND_TRY(dots(c, X, fs, j, x, h));
+        for (auto& v : h) v = -v;
+        ND_TRY(lincomb(c, x, 1.0, x, X, fs, j, h));
+      }
+      double n2;
+      ND_TRY(norm2_64(c, x, &n2));
+      if (n2 > 1e-200 && std::isfinite(n2)) {
+        ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0 / std::sqrt(n2), x, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+        break;
+      }
+      if (attempt == 2) return fail(c, ND_ERR_BREAKDOWN, "low modes: basis lost rank");
+      ND_TRY_CUDA(c, blas_random(c->g, x, 1000003ull * (j + 1) + attempt, c->stream));
+    }
+  }
+  return ND_OK;
+}
+
+// Rayleigh-Ritz of Q^2 on the orthonormal FP64 basis X (k fields): X <- X W, AX <- Q^2 X W,
+// theta ascending, res_i = ||Q^2 x_i - theta_i x_i||.
+nd_status rayleigh_ritz_q2(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size_t fs, std::vector<double>& theta,
+                           std::vector<double>& res) {
+  for (int j = 0; j < k; ++j) ND_TRY(apply_q2(c, AX + j * fs, X + j * fs));
+  std::vector<double> H(2 * k * k), h;
+  for (int j = 0; j < k; ++j) {
+    ND_TRY(dots(c, X, fs, k, AX + j * fs, h));
+    for (int i = 0; i < k; ++i) {
+      H[2 * (i * k + j)] = h[2 * i];
+      H[2 * (i * k + j) + 1] = h[2 * i + 1];
+    }
+  }
+  for (int i = 0; i < k; ++i)
+    for (int j = i; j < k; ++j) {
+      const double re = 0.5 * (H[2 * (i * k + j)] + H[2 * (j * k + i)]);
+      const double im = 0.5 * (H[2 * (i * k + j) + 1] - H[2 * (j * k + i) + 1]);
+      H[2 * (i * k + j)] = re;
+      H[2 * (i * k + j) + 1] = im;
+      H[2 * (j * k + i)] = re;
+      H[2 * (j * k + i) + 1] = -im;
+    }
+  std::vector<double> W;
+  hermitian_eig(k, H, theta, W);
+  // rotated basis into Y, rotated Q^2 X into X's old storage via a second pass
+  for (int j = 0; j < k; ++j) {
+    std::vector<double> coef(2 * k);
+    for (int i = 0; i < k; ++i) {
+      coef[2 * i] = W[2 * (i * k + j)];
+      coef[2 * i + 1] = W[2 * (i * k + j) + 1];
+    }
+    ND_TRY(lincomb(c, Y + j * fs, 0.0, nullptr, X, fs, k, coef));
+  }
+  std::swap(X, Y);  // X = rotated basis; Y = old basis (free)
+  for (int j = 0; j < k; ++j) {
+    std::vector<double> coef(2 * k);
+    for (int i = 0; i < k; ++i) {
+      coef[2 * i] = W[2 * (i * k + j)];
+      coef[2 * i + 1] = W[2 * (i * k + j) + 1];
+    }
+    ND_TRY(lincomb(c, Y + j * fs, 0.0, nullptr, AX, fs, k, coef));
+  }
+  std::swap(AX, Y);  // AX = rotated Q^2 X; Y free
+  res.assign(k, 0.0);
+  double* rs = c->red_scratch + 24;
+  void* tmp = field(c, "cf_res", 0);
+  if (!tmp) return fail(c, ND_ERR_OOM, "low modes: workspace");
+  for (int j = 0; j < k; ++j) {
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, tmp, 1.0, AX + j * fs, -theta[j], X + j * fs, true, slot(c, rs), c->stream));
+    double r2;
+    ND_TRY(read_back(c, rs, &r2, 1));
+    res[j] = std::sqrt(std::max(0.0, r2));
+  }
+  return ND_OK;
+}
+
+}  // namespace nd
+
+// Low modes by Chebyshev-filtered subspace iteration on Q^2: a block of k = l+1+buffer FP64
+// vectors is filtered with T_d(L(Q^2)) (damping [lo, lambda_max], lo = the largest Ritz value
+// of the block), re-orthonormalised in FP64 and Rayleigh-Ritz projected with FP64 Q^2.  The
+// filter runs in FP32 while the residuals are above 1e-5 lambda_max, then in FP64.
 extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double* nu_out, double* rho_out,
                                  double* evq2_out, nd_lowmode_info* info) {
   if (!c) return ND_ERR_INVALID_ARG;
@@ -232,88 +356,58 @@ extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double
   const size_t fs = (size_t)spinor_bytes(0, c->Vh);
   double lam_max;
   ND_TRY(lambda_max_estimate(c, 40, &lam_max));
-  c->lam_max = lam_max;
+  const double hi = 1.01 * lam_max;
   const int nwant = l + 1;
-  const int m = std::min(std::max(2 * nwant + 8, nwant + 20), 128);
-  const int keep = std::min(nwant + std::max(4, nwant / 2), m - 4);
-  char* V = static_cast<char*>(field(c, "lz_V", 0, m + 1));
-  char* W = static_cast<char*>(field(c, "lz_W", 0, m + 1));
-  if (!V || !W) return fail(c, ND_ERR_OOM, "nd_lowmodes: workspace");
-  ND_TRY_CUDA(c, blas_random(c->g, V, 777, c->stream));
-  double n2;
-  ND_TRY(norm2_64(c, V, &n2));
-  ND_TRY_CUDA(c, blas_axpby(c->g, 0, V, 1.0 / std::sqrt(n2), V, 0.0, nullptr, false, slot(c, nullptr), c->stream));
-  std::vector<double> T(2 * m * m, 0.0);
-  int k = 0, apps = 0;
-  std::vector<double> theta, Y;
-  double beta_m = 0.0;
+  // a block twice the wanted size keeps the damped interval away from the wanted modes when
+  // the low spectrum is a dense band (the gap between mode l+1 and the block edge sets the rate)
+  const int k = std::min(std::max(nwant + 8, 2 * nwant), 130);
+  char* X = static_cast<char*>(field(c, "cf_X", 0, k));
+  char* AX = static_cast<char*>(field(c, "cf_AX", 0, k));
+  char* Y = static_cast<char*>(field(c, "cf_Y", 0, k));
+  if (!X || !AX || !Y) return fail(c, ND_ERR_OOM, "nd_lowmodes: workspace");
+  for (int j = 0; j < k; ++j) ND_TRY_CUDA(c, blas_random(c->g, X + j * fs, 777 + 7919ull * j, c->stream));
+  ND_TRY(orthonormalise(c, X, k, fs));
+  std::vector<double> theta, res;
+  ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
+  int apps = k;
+  const bool trace = std::getenv("ND_TRACE") != nullptr;  // per-iteration progress on stderr
   bool converged = false;
-  for (;;) {
-    for (int j = k; j < m; ++j) {
-      void* w = V + (j + 1) * fs;
-      ND_TRY(apply_q2(c, w, V + j * fs));
-      ++apps;
-      std::vector<double> h, h2;
-      ND_TRY(dots(c, V, fs, j + 1, w, h));
-      std::vector<double> neg(2 * (j + 1));
-      for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h[i];
-      ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
-      ND_TRY(dots(c, V, fs, j + 1, w, h2));
-      for (int i = 0; i < 2 * (j + 1); ++i) neg[i] = -h2[i];
-      ND_TRY(lincomb(c, w, 1.0, w, V, fs, j + 1, neg));
-      for (int i = 0; i <= j; ++i) {
-        const double re = h[2 * i] + h2[2 * i], im = h[2 * i + 1] + h2[2 * i + 1];
-        if (i < k && j == k) {
-          // coupling of the kept Ritz vectors to the continuation vector
-          T[2 * (i * m + j)] = re;
-          T[2 * (i * m + j) + 1] = im;
-        } else if (i >= k || j > k) {
-          T[2 * (i * m + j)] = re;
-          T[2 * (i * m + j) + 1] = im;
-        }
-        T[2 * (j * m + i)] = T[2 * (i * m + j)];
-        T[2 * (j * m + i) + 1] = -T[2 * (i * m + j) + 1];
-      }
-      T[2 * (j * m + j) + 1] = 0.0;
-      double b2;
-      ND_TRY(norm2_64(c, w, &b2));
-      beta_m = std::sqrt(b2);
-      if (!(beta_m > 0) || !std::isfinite(beta_m)) return fail(c, ND_ERR_BREAKDOWN, "nd_lowmodes: Lanczos breakdown");
-      ND_TRY_CUDA(c, blas_axpby(c->g, 0, w, 1.0 / beta_m, w, 0.0, nullptr, false, slot(c, nullptr), c->stream));
-    }
-    std::vector<double> Tm = T;
-    hermitian_eig(m, Tm, theta, Y);
-    lam_max = std::max(lam_max, theta[m - 1]);
+  for (int it = 0; it < 1000; ++it) {
+    double worst = 0.0;
     int nconv = 0;
     for (int i = 0; i < nwant; ++i) {
-      const double res = beta_m * std::hypot(Y[2 * ((m - 1) * m + i)], Y[2 * ((m - 1) * m + i) + 1]);
-      if (res <= tol * lam_max) ++nconv;
+      worst = std::max(worst, res[i]);
+      if (res[i] <= tol * hi) ++nconv;
     }
-    converged = nconv == nwant;
-    const int kk = converged ? nwant : keep;
-    // Ritz vectors u_i = V Y[:, i] into W, then the continuation vector v_m
-    for (int i = 0; i < kk; ++i) {
-      std::vector<double> coef(2 * m);
-      for (int j = 0; j < m; ++j) {
-        coef[2 * j] = Y[2 * (j * m + i)];
-        coef[2 * j + 1] = Y[2 * (j * m + i) + 1];
-      }
-      ND_TRY(lincomb(c, W + i * fs, 0.0, nullptr, V, fs, m, coef));
+    if (nconv == nwant) {
+      converged = true;
+      break;
     }
-    if (converged || apps >= maxit) break;
-    ND_TRY_CUDA(c, cudaMemcpyAsync(W + kk * fs, V + m * fs, fs, cudaMemcpyDeviceToDevice, c->stream));
-    std::swap(V, W);
-    std::swap(c->ws["lz_V"], c->ws["lz_W"]);
-    std::fill(T.begin(), T.end(), 0.0);
-    for (int i = 0; i < kk; ++i) T[2 * (i * m + i)] = theta[i];
-    k = kk;
+    if (apps >= maxit) break;
+    const double lo = std::min(theta[k - 1], 0.5 * hi);
+    // FP32 filtering reaches residuals of about 1e-7 lambda_max; below 1e-6 lambda_max the
+    // filter switches to FP64 (needed only when tol asks for more than FP32 can give)
+    const int prec = (c->links[1] && worst > 1e-6 * hi) ? 1 : 0;
+    const int deg = prec == 1 ? 100 : 40;
+    if (trace)
+      std::fprintf(stderr, "nd_lowmodes: it %d apps %d filter fp%d lo %.6g hi %.6g theta0 %.6g theta_l %.6g worst %.3g nconv %d\n",
+                   it, apps, prec == 0 ? 64 : 32, lo, hi, theta[0], theta[l], worst, nconv);
+    for (int j = 0; j < k; ++j) ND_TRY(cheb_filter(c, prec, X + j * fs, deg, lo, hi));
+    apps += k * deg;
+    ND_TRY(orthonormalise(c, X, k, fs));
+    ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
+    apps += k;
+    lam_max = std::max(lam_max, theta[k - 1]);
   }
-  if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes: Lanczos did not converge within maxit");
-  // W holds the l+1 lowest Ritz vectors of Q^2; V = span of the first l
+  // keep the workspace registry pointing at the right buffers after the swaps
+  c->ws["cf_X"].first = X;
+  c->ws["cf_AX"].first = AX;
+  c->ws["cf_Y"].first = Y;
+  if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes: filtered subspace iteration did not converge");
   c->lam_next = theta[l];
   std::vector<double> nu, rho;
-  ND_TRY(ritz_of_Q(c, W, l, nu, rho));
-  ND_TRY(store_modes(c, W, l));
+  ND_TRY(ritz_of_Q(c, X, l, nu, rho));
+  ND_TRY(store_modes(c, X, l));
   c->nu = nu;
   c->rho = rho;
   double kp, km;

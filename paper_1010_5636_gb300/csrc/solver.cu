@@ -11,17 +11,19 @@
 namespace nd {
 
 nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a, double b, const void* y, double* result,
-                  const double* cgs) {
+                  const double* cgs, const void* z, double cz) {
   if (!c->links[prec]) return fail(c, ND_ERR_STATE, "links are not set in the precision this call needs");
   QLaunch L{};
   L.prec = prec;
   L.recon = c->recon[prec];
-  L.mode = Q_PLAIN;
+  L.mode = z ? Q_XPAY2 : Q_PLAIN;
   L.reduce = result != nullptr;
   L.links = c->links[prec];
   L.in = in;
   L.out = out;
   L.y = y;
+  L.z = z;
+  L.c = cz;
   L.diag = 4.0 + c->m;
   L.a = a;
   L.b = b;

@@ -6,10 +6,11 @@
 
 namespace nd {
 
-// out = a * Q in + b * y (internal fields of precision prec).  With result != null the launch
+// out = a * Q in + b * y + cz * z (internal fields of precision prec; z may alias out).  With result != null the launch
 // also reduces ||out||^2 and ||in||^2 into result[0..1].
 nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a = 1.0, double b = 0.0,
-                  const void* y = nullptr, double* result = nullptr, const double* cgs = nullptr);
+                  const void* y = nullptr, double* result = nullptr, const double* cgs = nullptr,
+                  const void* z = nullptr, double cz = 0.0);
 
 // Device buffer for one internal field of `prec`, cached under `name`.
 void* field(nd_ctx* c, const char* name, int prec, int count = 1);

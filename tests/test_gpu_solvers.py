@@ -93,7 +93,7 @@ def test_lowmodes_vs_dense(nd, cfg1):
         assert np.allclose(np.sort(nu), np.sort(lm["nu"]), rtol=1e-9, atol=1e-12)
         # a Ritz value from below; sign(Q) pads it by 1 %
         assert lm["lam_max"] * (1 - 2e-3) <= info.lambda_max <= lm["lam_max"] * (1 + 1e-12)
-        assert max(rho) < 1e-9 and info.kappa_plus < 1e-7 and info.kappa_minus < 1e-7
+        assert max(rho) < 1e-9 and info.kappa_plus < 1e-6 and info.kappa_minus < 1e-6
         import torch
         ev_dev = torch.empty((l,) + eta.shape, dtype=torch.complex128, device="cuda")
         nu2 = nd.nd_get_lowmodes(ctx, ev_dev, l)
