@@ -116,6 +116,17 @@ nd_status nd_apply_Q_parity(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_p
 /* Convenience: Q on canonical FP64 device spinors (packs, applies in FP64, unpacks). */
 nd_status nd_apply_Q_canonical(nd_ctx* ctx, double* out_dev, const double* in_dev);
 
+/* out = Q in as nd_apply_Q (nrhs = 1), and norms[0] = ||out||^2, norms[1] = ||in||^2 (host,
+ * FP64), for callers that may not allocate device memory at call time (a fixed memory budget
+ * owned by another allocator, or a loop that promised no allocation after set-up).  The paper
+ * has no counterpart; this is a library-service variant of the fused-norm launch.
+ * It allocates nothing: the reduction scratch is a static device array of 256 KiB per GPU
+ * (kept until exit), which limits the lattice to 4194304 sites (larger: ND_ERR_INVALID_ARG).
+ * The first call on a device looks up that array's device address; make it before any
+ * stream capture.  All calls share the array: calls that overlap on the GPU race on it.
+ * Synchronises the context's stream. */
+nd_status nd_apply_Q_norms_static(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec, double* norms);
+
 /* ---------------------------------------------------------------- solvers */
 
 typedef struct {

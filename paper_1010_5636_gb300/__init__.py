@@ -66,6 +66,7 @@ _SIGS = {
     "nd_apply_Q": ([_P, _P, _P, _I, _I], _I),
     "nd_apply_Q_parity": ([_P, _P, _P, _I, _I, _D], _I),
     "nd_apply_Q_canonical": ([_P, _P, _P], _I),
+    "nd_apply_Q_norms_static": ([_P, _P, _P, _I, _P], _I),
     "nd_solve": ([_P, _P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_lowmodes": ([_P, _I, _D, _I, _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
     "nd_set_lowmodes": ([_P, _I, _P, _P, _D, ctypes.POINTER(nd_lowmode_info)], _I),
@@ -184,6 +185,14 @@ def nd_apply_Q_parity(ctx, out, inp, prec, parity, diag_coef):
 
 def nd_apply_Q_canonical(ctx, out, inp):
     _check(ctx, lib().nd_apply_Q_canonical(ctx, _ptr(_f64(out)), _ptr(_f64(inp))), "nd_apply_Q_canonical")
+
+
+def nd_apply_Q_norms_static(ctx, out, inp, prec):
+    """Q with fused norms and no device allocation (static scratch); returns (||out||^2, ||in||^2)."""
+    norms = (ctypes.c_double * 2)()
+    _check(ctx, lib().nd_apply_Q_norms_static(ctx, _ptr(out), _ptr(inp), int(prec), ctypes.cast(norms, _P)),
+           "nd_apply_Q_norms_static")
+    return norms[0], norms[1]
 
 
 def nd_solve(ctx, xs, b, shifts, tol, maxit=100000, inner=ND_FP64):
