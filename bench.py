@@ -392,6 +392,26 @@ def dn_phase(nd, torch, reps):
     return res
 
 
+def profile_case(nd, torch, case):
+    """Small cases for ncu captures (a few launches, a few hundred MB on the device)."""
+    import synth
+    if case == "hop24":
+        dims = (48, 24, 24, 24)
+        U = torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda()
+        ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+        nd.nd_set_links(ctx, U, (0, RECON, 0))
+        a = torch.empty(nd.nd_spinor_bytes(ctx, 1), dtype=torch.uint8, device="cuda")
+        b = torch.empty_like(a)
+        nd.nd_pack_spinor(ctx, a, torch.from_numpy(synth.spinor(dims, seed=1)).cuda(), 1)
+        for _ in range(3):
+            nd.nd_apply_Q_parity(ctx, b, a, 1, 0, 0.0)
+        torch.cuda.synchronize()
+        nd.nd_destroy(ctx)
+    else:
+        raise SystemExit(f"unknown case {case}")
+    print(json.dumps({"case": case, "ok": True}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,9 +422,17 @@ def main():
     ap.add_argument("--no-dn", action="store_true")
     ap.add_argument("--dn-reps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--case", default=None, help="run a small profiling case and exit (hop24)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.case:
+        import torch
+
+        import paper_1010_5636_gb300 as nd
+        nd.lib(build_if_missing=False)
+        profile_case(nd, torch, args.case)
+        return 0
     world, rank, local = dist_setup(args)
     import torch
 
@@ -417,14 +445,14 @@ def main():
     peaks, src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = d["per_launch_bytes"] / (d["avg_launch_ms"] * 1e-3) / 1e9
+    # DRAM bytes of one launch from the committed ncu capture of this kernel (24^3x48 case scaled
+    # to this lattice by the number of sites); null if the summary is missing
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", "dslash_traffic.json")
+    tfile = os.path.join(ROOT, "profiles", "dslash_hop_24x48_fp32r12.md")
     if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            traffic = tj.get("dram_bytes_per_launch_scaled")
-        except Exception:
-            traffic = None
+        for ln in open(tfile):
+            if ln.startswith("traffic_bytes_per_launch_64x32c:"):
+                traffic = int(ln.split(":")[1])
     line = {
         "metric": METRIC, "value": round(d["gbs"], 1), "unit": "GB/s", "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": round(d["total_ms"] / steps, 4), "higher_is_better": True, "scaling": "weak",

@@ -59,6 +59,8 @@ struct QLaunch {
   ReduceSlot slot;
   const double* cgs;  // multi-shift CG scalars, or null; kernels skip when cgs[CG_DONE] or cgs[CG_PENDING] != 0
   int split;          // warps per site: 1, 2 or 4 (0 = default for the precision)
+  int threads;        // 0: default block shape; 256: 256-thread blocks (callers that size
+                      // per-block scratch for 256 sites per block)
 };
 int default_split(int prec, int recon, bool half);
 

@@ -80,7 +80,8 @@ extern "C" nd_status nd_apply_Q_norms_static(nd_ctx* c, void* out, const void* i
   L.diag = 4.0 + c->m;
   L.a = 1.0;
   L.nsites = (int)c->V;
-  L.split = 1;  // 256 sites per block: the partials fit the static array
+  L.split = 1;
+  L.threads = 256;  // 256 sites per block: the partials fit the static array
   L.slot.result = s;
   L.slot.counter = reinterpret_cast<unsigned*>(s + 2);
   L.slot.partials = s + 8;
