@@ -129,6 +129,11 @@ void nd_destroy(nd_ctx* c) {
   if (c->stream || true) cudaStreamSynchronize(c->stream);
   for (int k = 0; k < 3; ++k)
     if (c->links[k]) cudaFree(c->links[k]);
+  for (auto& gr : c->ms_graphs) {
+    if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    if (gr.graph) cudaGraphDestroy(gr.graph);
+  }
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   if (c->evecs) cudaFree(c->evecs);
   if (c->red_partials) cudaFree(c->red_partials);
@@ -221,23 +226,28 @@ nd_status nd_apply_Q(nd_ctx* c, void* out, const void* in, nd_prec prec, int nrh
   if (out == in) return fail(c, ND_ERR_INVALID_ARG, "nd_apply_Q: out and in must not overlap");
   if (!c->links[prec]) return fail(c, ND_ERR_STATE, "nd_apply_Q: no links set in this precision");
   const size_t sb = nd_spinor_bytes(c, prec);
-  for (int k = 0; k < nrhs; ++k) {
-    QLaunch L{};
-    L.prec = (int)prec;
-    L.recon = c->recon[prec];
-    L.mode = Q_PLAIN;
-    L.reduce = false;
-    L.links = c->links[prec];
-    L.in = static_cast<const char*>(in) + k * sb;
-    L.out = static_cast<char*>(out) + k * sb;
-    L.y = nullptr;
-    L.diag = 4.0 + c->m;
-    L.a = 1.0;
-    L.b = 0.0;
-    L.parity0 = 0;
-    L.nsites = (int)c->V;
+  const char* ib = static_cast<const char*>(in);
+  const char* ob = static_cast<const char*>(out);
+  if (ib < ob + nrhs * sb && ob < ib + nrhs * sb)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_apply_Q: out and in must not overlap");
+  QLaunch L{};
+  L.prec = (int)prec;
+  L.recon = c->recon[prec];
+  L.mode = Q_PLAIN;
+  L.reduce = false;
+  L.links = c->links[prec];
+  L.in = in;
+  L.out = out;
+  L.y = nullptr;
+  L.diag = 4.0 + c->m;
+  L.a = 1.0;
+  L.b = 0.0;
+  L.parity0 = 0;
+  L.nsites = (int)c->V;
+  if (nrhs == 1)
     ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
-  }
+  else
+    ND_TRY_CUDA(c, launch_q_mrhs(c->g, L, nrhs, sb, c->stream));  // links read once for all RHS
   return ND_OK;
 }
 

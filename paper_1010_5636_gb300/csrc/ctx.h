@@ -11,6 +11,15 @@
 
 constexpr int ND_PINNED_DOUBLES = 4096;
 
+// One multi-shift CG solve captured as a CUDA graph: a device-side while loop whose body is one
+// iteration (four kernels); reused while every buffer pointer and size in the key matches.
+struct nd_ms_graph {
+  int ps = 0, px = 0, ymode = 0, n = 0, maxit = 0;
+  const void *r = nullptr, *t = nullptr, *p = nullptr, *x = nullptr, *state = nullptr, *links = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 struct nd_ctx {
   nd::Geom g;
   int dims[4];
@@ -37,6 +46,10 @@ struct nd_ctx {
   size_t evecs_cap = 0;
   std::vector<double> nu, rho;
   double lam_next = 0.0, lam_max = 0.0;
+  // captured multi-shift iterations (graphs_ok = false after a capture failure: chunked launches)
+  cudaStream_t cap_stream = nullptr;
+  std::vector<nd_ms_graph> ms_graphs;
+  bool graphs_ok = true;
 };
 
 namespace nd {

@@ -26,10 +26,23 @@ int default_split(int prec, int recon, bool half) {
   return 1;
 }
 
+cudaError_t launch_q_mrhs(const Geom& g, const QLaunch& L0, int nrhs, size_t stride, cudaStream_t st) {
+  if (L0.mode != Q_PLAIN || L0.reduce) return cudaErrorInvalidValue;
+  QLaunch L = L0;
+  L.mode = Q_MRHS;
+  L.nrhs = nrhs;
+  L.rhs_stride = (int64_t)stride;
+  L.split = 1;
+  L.threads = 0;
+  return launch_q(g, L, st);
+}
+
 cudaError_t launch_q(const Geom& g, const QLaunch& L0, cudaStream_t st) {
   if (L0.nsites <= 0) return cudaSuccess;
   QLaunch L = L0;
+  if (L.mode == Q_MRHS && (L.nrhs < 1 || L.reduce)) return cudaErrorInvalidValue;
   if (L.split == 0) L.split = default_split(L.prec, L.recon, L.nsites != 2 * g.Vh);
+  if (L.mode == Q_MRHS) L.split = 1;
   switch (L.prec) {
     case 0: return launch_q_fp64(g, L, st);
     case 1: return launch_q_fp32(g, L, st);

@@ -45,14 +45,24 @@ __device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& a
 }
 
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS = Q_THREADS, int MINB = 1>
-__global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A) {
+__global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A0) {
   using T = typename Traits<P>::real;
-  if (A.cgs && (A.cgs[CG_DONE] != 0.0 || A.cgs[CG_PENDING] != 0.0)) return;
+  if (A0.cgs && (A0.cgs[CG_DONE] != 0.0 || A0.cgs[CG_PENDING] != 0.0)) return;
   constexpr int SITES = THREADS / SPLIT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = SPLIT == 1 ? 0 : warp % SPLIT;
   const int jloc = (warp / SPLIT) * 32 + lane;
-  const int i = blockIdx.x * SITES + jloc;
+  int blk = blockIdx.x;
+  QLaunch A = A0;
+  if constexpr (MODE == Q_MRHS) {
+    // several right-hand sides: consecutive blocks take the same sites for successive RHS
+    const int r = blk % A.nrhs;
+    blk /= A.nrhs;
+    A.in = static_cast<const char*>(A.in) + r * A.rhs_stride;
+    A.out = static_cast<char*>(A.out) + r * A.rhs_stride;
+    if (A.y) A.y = static_cast<const char*>(A.y) + r * A.rhs_stride;
+  }
+  const int i = blk * SITES + jloc;
   const bool act = i < A.nsites;
   int p = 0, h = 0;
   if (A.nsites == 2 * g.Vh) {
@@ -94,13 +104,17 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
       }
   }
   double red[2] = {0.0, 0.0};
-  const T diag = (T)A.diag, ca = (T)A.a, cb = (T)A.b;
+  // in the CG mode the operator scale and the base shift come from the solver state, so one
+  // captured launch serves every solve
+  const double a_d = MODE == Q_CGUPDATE ? A.cgs[CG_ASCALE] : A.a;
+  const double b_d = MODE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
+  const T diag = (T)A.diag, ca = (T)a_d, cb = (T)b_d;
   const bool read_diag = REDUCE || A.diag != 0.0;
   constexpr bool IN_PLACE = MODE == Q_CGUPDATE || MODE == Q_XPAY2;
   Spinor<T> d, y, z;
   if (act) {
     if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
-    if (MODE != Q_PLAIN || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
+    if ((MODE != Q_PLAIN && MODE != Q_MRHS) || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
     if (MODE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
     if (MODE == Q_XPAY2) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
   }
@@ -118,7 +132,7 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
         v = (a < 2 ? ca : -ca) * v;  // gamma5 = diag(1, 1, -1, -1)
         res.s[a][c] = v;
       }
-    if (MODE == Q_PLAIN) {
+    if (MODE == Q_PLAIN || MODE == Q_MRHS) {
       if (A.y) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
@@ -132,7 +146,7 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
 #pragma unroll
         for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c] + cc * z.s[a][c];
     } else {
-      const double alpha = A.cgs[CG_RR] / (A.a * A.cgs[CG_TT] + A.b * A.cgs[CG_PP]);
+      const double alpha = A.cgs[CG_RR] / (a_d * A.cgs[CG_TT] + b_d * A.cgs[CG_PP]);
       const T al = (T)alpha;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -160,7 +174,7 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS, int MINB>
 static cudaError_t launch_q5(const Geom& g, const QLaunch& L, cudaStream_t st) {
   constexpr int SITES = THREADS / SPLIT;
-  const int blocks = (L.nsites + SITES - 1) / SITES;
+  const int blocks = (L.nsites + SITES - 1) / SITES * (L.nrhs > 1 ? L.nrhs : 1);
   const size_t smem = SPLIT > 1 ? (size_t)SPLIT * 24 * SITES * sizeof(typename Traits<P>::real) : 0;
   static bool attr = false;
   if (smem > 48 * 1024 && !attr) {
@@ -197,6 +211,10 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
       return L.reduce ? launch_q4<P, R, Q_XPAY2, true>(g, L, st) : launch_q4<P, R, Q_XPAY2, false>(g, L, st);
     case Q_CGUPDATE:
       return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
+    case Q_MRHS:
+      if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
+      if (P == P64) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
+      return launch_q5<P, R, Q_MRHS, false, 1, 64, 8>(g, L, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -36,12 +36,13 @@ constexpr int CG_NMAX = 32;
 constexpr int CG_STATE_DOUBLES = CG_NSCALAR + SH_NARRAY * CG_NMAX;
 __host__ __device__ inline int sh(int array, int l) { return CG_NSCALAR + array * CG_NMAX + l; }
 
-enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2 };
+enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2, Q_MRHS = 3 };  // Q_MRHS: Q_PLAIN over nrhs fields
 
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y      (Q_PLAIN; y may be null)
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y + c * z   (Q_XPAY2; z may alias out)
 // out = out - alpha * (a * gamma5(diag * in - 1/2 hop(in)) + b * y),
-//       alpha = cgs[CG_RR] / (a * cgs[CG_TT] + b * cgs[CG_PP])      (Q_CGUPDATE)
+//       alpha = cgs[CG_RR] / (a * cgs[CG_TT] + b * cgs[CG_PP]),
+//       a = cgs[CG_ASCALE], b = cgs[CG_SIGMA0]                       (Q_CGUPDATE)
 // Output sites: parity `parity0` only (nsites = Vh) or both parities (nsites = 2 Vh).
 // reduce: slot.result[0] = sum ||out||^2, slot.result[1] = sum ||in||^2 over the output sites.
 struct QLaunch {
@@ -61,10 +62,17 @@ struct QLaunch {
   int split;          // warps per site: 1, 2 or 4 (0 = default for the precision)
   int threads;        // 0: default block shape; 256: 256-thread blocks (callers that size
                       // per-block scratch for 256 sites per block)
+  int nrhs;           // right-hand sides in one launch (0 or 1: one)
+  int64_t rhs_stride; // bytes between consecutive RHS fields
 };
 int default_split(int prec, int recon, bool half);
 
 cudaError_t launch_q(const Geom& g, const QLaunch& L, cudaStream_t st);
+// The same operator on nrhs fields at in + r * stride (out, y likewise), one launch: the RHS
+// index is the fastest-varying block index, so the blocks that read one tile of links for all
+// RHS run back to back and the links come from DRAM once (Q_PLAIN, no reduction, one warp per
+// site).
+cudaError_t launch_q_mrhs(const Geom& g, const QLaunch& L, int nrhs, size_t stride, cudaStream_t st);
 
 // Pack / unpack between canonical FP64 ([lex][4][3][2]) and internal precision `prec`.
 cudaError_t launch_pack_spinor(const Geom& g, int prec, void* internal, const double* canon, cudaStream_t st);
@@ -103,6 +111,9 @@ cudaError_t blas_random(const Geom& g, void* out, uint64_t seed, cudaStream_t st
 // ---------------------------------------------------------------- multi-shift CG (mscg.cu)
 cudaError_t mscg_init(double* state, int n, cudaStream_t st);
 cudaError_t mscg_scalar(double* state, int n, int maxit, cudaStream_t st);
+// The same step inside a CUDA graph whose while-loop runs the iterations: when the run stops
+// the kernel sets the loop's condition to zero.
+cudaError_t mscg_scalar_graph(double* state, int n, int maxit, cudaGraphConditionalHandle h, cudaStream_t st);
 // For every live shift l (x_l / p_l at base + l * stride): x_l += coefx_l p_l (or y += w_l coefx_l p_l
 // when ymode), p_l = coefr_l r + coefp_l p_l.
 cudaError_t mscg_update(const Geom& g, int prec_s, int prec_x, bool ymode, const void* r, void* p_all, size_t pstride,

@@ -52,12 +52,15 @@ __global__ void mscg_init_kernel(double* s, int n) {
   }
 }
 
-__global__ void mscg_scalar_kernel(double* s, int n, int maxit) {
-  if (s[CG_DONE] != 0.0) return;
-  if (s[CG_PENDING] != 0.0) {
+template <bool GRAPH>
+__global__ void mscg_scalar_kernel(double* s, int n, int maxit, cudaGraphConditionalHandle h) {
+  if (s[CG_DONE] != 0.0 || s[CG_PENDING] != 0.0) {
     // the update of the iteration that set PENDING has been applied: stop everything now,
     // so the update kernels of further (already launched) iterations skip as well
-    if (threadIdx.x == 0) s[CG_DONE] = 1.0;
+    if (threadIdx.x == 0) {
+      s[CG_DONE] = 1.0;
+      if (GRAPH) cudaGraphSetConditional(h, 0);
+    }
     return;
   }
   const int l = threadIdx.x;
@@ -111,6 +114,8 @@ __global__ void mscg_scalar_kernel(double* s, int n, int maxit) {
       s[CG_PENDING] = 1.0;
       s[CG_STATUS] = (double)ND_ERR_NOT_CONVERGED;
     }
+    // in a graph the while-loop ends after this iteration's update kernel
+    if (GRAPH && (s[CG_DONE] != 0.0 || s[CG_PENDING] != 0.0)) cudaGraphSetConditional(h, 0);
   }
 }
 
@@ -171,7 +176,12 @@ cudaError_t mscg_init(double* state, int n, cudaStream_t st) {
 }
 
 cudaError_t mscg_scalar(double* state, int n, int maxit, cudaStream_t st) {
-  mscg_scalar_kernel<<<1, CG_NMAX, 0, st>>>(state, n, maxit);
+  mscg_scalar_kernel<false><<<1, CG_NMAX, 0, st>>>(state, n, maxit, cudaGraphConditionalHandle{});
+  return cudaGetLastError();
+}
+
+cudaError_t mscg_scalar_graph(double* state, int n, int maxit, cudaGraphConditionalHandle h, cudaStream_t st) {
+  mscg_scalar_kernel<true><<<1, CG_NMAX, 0, st>>>(state, n, maxit, h);
   return cudaGetLastError();
 }
 

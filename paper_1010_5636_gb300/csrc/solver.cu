@@ -4,6 +4,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
 #include <numeric>
 
 #include "solver.h"
@@ -49,6 +52,96 @@ nd_status read_back(nd_ctx* c, const double* dev, double* host, int n) {
   return ND_OK;
 }
 
+// One multi-shift CG iteration (K1..K4, see mscg.cu) launched on stream st; with graph != null
+// the scalar kernel also drives the graph's while-loop condition.
+static cudaError_t ms_iteration(nd_ctx* c, cudaStream_t st, int ps, int px, bool ymode, void* r, void* t, char* p_all,
+                                size_t fs, void* x_or_y, size_t fx, double* state, int n, int maxit,
+                                const cudaGraphConditionalHandle* graph) {
+  QLaunch L1{};
+  L1.prec = ps;
+  L1.recon = c->recon[ps];
+  L1.mode = Q_PLAIN;
+  L1.reduce = true;
+  L1.links = c->links[ps];
+  L1.in = p_all;
+  L1.out = t;
+  L1.diag = 4.0 + c->m;
+  L1.a = 1.0;
+  L1.nsites = (int)c->V;
+  L1.slot = slot(c, state + CG_TT);
+  L1.cgs = state;
+  cudaError_t e = launch_q(c->g, L1, st);
+  if (e != cudaSuccess) return e;
+  QLaunch L2 = L1;
+  L2.mode = Q_CGUPDATE;
+  L2.in = t;
+  L2.out = r;
+  L2.y = p_all;
+  L2.slot = slot(c, state + CG_RRNEW);
+  e = launch_q(c->g, L2, st);
+  if (e != cudaSuccess) return e;
+  e = graph ? mscg_scalar_graph(state, n, maxit, *graph, st) : mscg_scalar(state, n, maxit, st);
+  if (e != cudaSuccess) return e;
+  return mscg_update(c->g, ps, px, ymode, r, p_all, fs, ymode ? nullptr : x_or_y, fx, ymode ? x_or_y : nullptr,
+                     state, n, st);
+}
+
+// Find or capture the graph of a solve with these buffers; null if graphs are unavailable.
+static nd_ms_graph* ms_graph(nd_ctx* c, int ps, int px, bool ymode, void* r, void* t, char* p_all, size_t fs,
+                             void* x_or_y, size_t fx, double* state, int n, int maxit) {
+  if (!c->graphs_ok) return nullptr;
+  for (auto& gr : c->ms_graphs)
+    if (gr.ps == ps && gr.px == px && gr.ymode == (int)ymode && gr.n == n && gr.maxit == maxit && gr.r == r &&
+        gr.t == t && gr.p == p_all && gr.x == x_or_y && gr.state == state && gr.links == c->links[ps])
+      return &gr;
+  nd_ms_graph G;
+  G.ps = ps, G.px = px, G.ymode = ymode, G.n = n, G.maxit = maxit;
+  G.r = r, G.t = t, G.p = p_all, G.x = x_or_y, G.state = state, G.links = c->links[ps];
+  bool ok = true;
+  cudaGraphConditionalHandle h{};
+  cudaGraphNode_t node;
+  // cudaGraphNodeParams has no default constructor (a union of parameter blocks): zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+  memset(cp_raw, 0, sizeof(cp_raw));
+  cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+  ok = ok && cudaGraphCreate(&G.graph, 0) == cudaSuccess;
+  ok = ok && cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok) {
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    ok = cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  }
+  if (ok && !c->cap_stream) ok = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      const cudaError_t e1 = ms_iteration(c, c->cap_stream, ps, px, ymode, r, t, p_all, fs, x_or_y, fx, state, n,
+                                          maxit, &h);
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &body);
+      ok = e1 == cudaSuccess && e2 == cudaSuccess;
+    }
+  }
+  ok = ok && cudaGraphInstantiate(&G.exec, G.graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    c->graphs_ok = false;  // fall back to launches from the host from now on
+    return nullptr;
+  }
+  if (c->ms_graphs.size() >= 32) {
+    cudaGraphExecDestroy(c->ms_graphs.front().exec);
+    cudaGraphDestroy(c->ms_graphs.front().graph);
+    c->ms_graphs.erase(c->ms_graphs.begin());
+  }
+  c->ms_graphs.push_back(G);
+  return &c->ms_graphs.back();
+}
+
 nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x_or_y, const std::vector<double>& sigma,
                    const std::vector<double>& tol, const std::vector<double>& w, double ascale, int maxit,
                    MsResult* out) {
@@ -75,38 +168,24 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
   for (int l = 0; l < n; ++l) ND_TRY_CUDA(c, cudaMemcpyAsync(p_all + l * fs, b, fs, cudaMemcpyDeviceToDevice, c->stream));
   ND_TRY_CUDA(c, cudaMemsetAsync(x_or_y, 0, ymode ? fx : fx * n, c->stream));
   ND_TRY_CUDA(c, mscg_init(state, n, c->stream));
-  const double s0 = sigma[0];
-  int chunk = 8;
   double hs[CG_NSCALAR];
-  for (;;) {
-    for (int k = 0; k < chunk; ++k) {
-      // K1: t = Q p_0, (||t||^2, ||p_0||^2) -> (TT, PP)
-      ND_TRY(q_apply(c, ps, t, p_all, 1.0, 0.0, nullptr, state + CG_TT, state));
-      // K2: r -= alpha (ascale Q t + sigma_0 p_0), ||r||^2 -> RRNEW
-      QLaunch L{};
-      L.prec = ps;
-      L.recon = c->recon[ps];
-      L.mode = Q_CGUPDATE;
-      L.reduce = true;
-      L.links = c->links[ps];
-      L.in = t;
-      L.out = r;
-      L.y = p_all;
-      L.diag = 4.0 + c->m;
-      L.a = ascale;
-      L.b = s0;
-      L.nsites = (int)c->V;
-      L.slot = slot(c, state + CG_RRNEW);
-      L.cgs = state;
-      ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
-      // K3, K4
-      ND_TRY_CUDA(c, mscg_scalar(state, n, maxit, c->stream));
-      ND_TRY_CUDA(c, mscg_update(c->g, ps, px, ymode, r, p_all, fs, ymode ? nullptr : x_or_y, fx,
-                                 ymode ? x_or_y : nullptr, state, n, c->stream));
-    }
+  if (!c->links[ps]) return fail(c, ND_ERR_STATE, "multi-shift CG: links not set in the Krylov precision");
+  nd_ms_graph* G = ms_graph(c, ps, px, ymode, r, t, p_all, fs, x_or_y, fx, state, n, maxit);
+  if (G) {
+    // the whole solve is one graph launch: the iterations loop on the device until the scalar
+    // kernel ends the while-loop
+    ND_TRY_CUDA(c, cudaGraphLaunch(G->exec, c->stream));
     ND_TRY(read_back(c, state, hs, CG_NSCALAR));
-    if (hs[CG_DONE] != 0.0 || hs[CG_PENDING] != 0.0) break;
-    chunk = std::min(chunk * 2, 64);
+  } else {
+    int chunk = 8;
+    for (;;) {
+      for (int k = 0; k < chunk; ++k)
+        ND_TRY_CUDA(c, ms_iteration(c, c->stream, ps, px, ymode, r, t, p_all, fs, x_or_y, fx, state, n, maxit,
+                                    nullptr));
+      ND_TRY(read_back(c, state, hs, CG_NSCALAR));
+      if (hs[CG_DONE] != 0.0 || hs[CG_PENDING] != 0.0) break;
+      chunk = std::min(chunk * 2, 64);
+    }
   }
   std::vector<double> res(n);
   ND_TRY(read_back(c, state + sh(SH_RES, 0), res.data(), n));
@@ -144,8 +223,13 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
                            nd_status (*sink)(void*, int, void*), void* sink_ctx) {
   const int n = (int)sigma.size();
   // Sloppy pass: the Krylov vectors in ps, the shifted solutions in FP32.
-  const double floor_s = ps == 2 ? 1e-3 : 1e-6;   // where the sloppy recurrence stops being trusted
-  const double floor_in = ps == 2 ? 1e-5 : 1e-5;  // inner reduction per refinement step (FP32 solves)
+  // floor_s: where the sloppy multi-shift recurrence stops being trusted; floor_in: the smallest
+  // reduction asked of one FP32 correction solve.  ND_MIXED_FLOOR_S / ND_MIXED_FLOOR_IN in the
+  // environment override them (tuning).
+  double floor_s = ps == 2 ? 1e-3 : 1e-6;
+  double floor_in = 1e-5;
+  if (const char* e = std::getenv("ND_MIXED_FLOOR_S")) floor_s = std::atof(e);
+  if (const char* e = std::getenv("ND_MIXED_FLOOR_IN")) floor_in = std::atof(e);
   void* bS = field(c, "mx_bS", ps);
   char* x32 = static_cast<char*>(field(c, "mx_x32", 1, n));
   void* x64 = field(c, "mx_x64", 0);
@@ -165,10 +249,11 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   const size_t f32 = (size_t)spinor_bytes(1, c->Vh);
   for (int l = 0; l < n; ++l) {
     ND_TRY_CUDA(c, blas_convert(c->g, 0, x64, 1, x32 + l * f32, c->stream));
-    double rel = 0.0;
+    double rel = 0.0, first_rel = -1.0;
     int outer = 0;
     for (;;) {
       ND_TRY(residual64(c, r64, b64, x64, sigma[l], ascale, bnorm2, &rel));
+      if (first_rel < 0) first_rel = rel;
       if (rel <= tol[l]) break;
       if (outer >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
       ++outer;
@@ -183,6 +268,9 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
       ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, e32, c->stream));
       ND_TRY_CUDA(c, blas_axpby(c->g, 0, x64, 1.0, x64, 1.0, r64, false, slot(c, nullptr), c->stream));
     }
+    if (std::getenv("ND_TRACE"))
+      std::fprintf(stderr, "mixed solve: shift %d sigma %.3e sloppy resid %.3e outer %d final %.3e\n", l, sigma[l],
+                   first_rel, outer, rel);
     st->outer = std::max(st->outer, outer);
     st->max_resid = std::max(st->max_resid, rel);
     ND_TRY(sink(sink_ctx, l, x64));

@@ -163,3 +163,52 @@ def test_Q_canonical(nd):
         assert rel(host(out), wilson.apply_Q(U, psi, dims, M)) <= 1e-12
     finally:
         nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,recon", [(0, 18), (1, 12), (1, 18), (2, 12)])
+@pytest.mark.parametrize("nrhs", [2, 5, 12])
+def test_Q_multi_rhs(nd, prec, recon, nrhs):
+    """nrhs fields in one launch (links shared) equal nrhs single applications and the oracle."""
+    import torch
+    dims = (6, 4, 4, 6)
+    V = int(np.prod(dims))
+    U = synth.gauge_field(dims, "haar", seed=0)
+    psi = synth.spinor(dims, seed=3, nrhs=nrhs)
+    ctx = nd.nd_create(dims, m=M)
+    try:
+        rc = [0, 0, 0]
+        rc[prec] = recon
+        nd.nd_set_links(ctx, dev(U), rc)
+        sb = nd.nd_spinor_bytes(ctx, prec)
+        inb = torch.empty(sb * nrhs, dtype=torch.uint8, device="cuda")
+        nd.nd_pack_spinor(ctx, inb, dev(psi), prec, nrhs)
+        outb = torch.empty_like(inb)
+        nd.nd_apply_Q(ctx, outb, inb, prec, nrhs)
+        one = torch.empty_like(inb)
+        for r in range(nrhs):
+            nd.nd_apply_Q(ctx, one[r * sb:(r + 1) * sb], inb[r * sb:(r + 1) * sb], prec, 1)
+        got = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device="cuda")
+        ref = torch.empty_like(got)
+        nd.nd_unpack_spinor(ctx, got, outb, prec, nrhs)
+        nd.nd_unpack_spinor(ctx, ref, one, prec, nrhs)
+        torch.cuda.synchronize()
+        assert rel(host(got), host(ref)) <= (1e-15 if prec == 0 else 1e-6)
+        exp = wilson.apply_Q(U, psi, dims, M)
+        assert rel(host(got), exp) <= TOL[prec]
+    finally:
+        nd.nd_destroy(ctx)
+
+
+def test_Q_multi_rhs_overlap_rejected(nd):
+    import torch
+    dims = (4, 4, 4, 4)
+    ctx = nd.nd_create(dims, m=M)
+    try:
+        nd.nd_set_links(ctx, dev(synth.gauge_field(dims, "haar", seed=0)), (0, 12, 0))
+        sb = nd.nd_spinor_bytes(ctx, 1)
+        buf = torch.zeros(sb * 3, dtype=torch.uint8, device="cuda")
+        with pytest.raises(nd.NdError) as e:
+            nd.nd_apply_Q(ctx, buf[sb:], buf[:2 * sb], 1, 2)
+        assert e.value.status == nd.ND_ERR_INVALID_ARG
+    finally:
+        nd.nd_destroy(ctx)
