@@ -14,6 +14,7 @@ constexpr int ND_PINNED_DOUBLES = 4096;
 // One multi-shift CG solve captured as a CUDA graph: a device-side while loop whose body is one
 // iteration (four kernels); reused while every buffer pointer and size in the key matches.
 struct nd_ms_graph {
+  int kind = 0;  // 0: multi-shift CG, 1: batched CG
   int ps = 0, px = 0, ymode = 0, n = 0, maxit = 0;
   const void *r = nullptr, *t = nullptr, *p = nullptr, *x = nullptr, *state = nullptr, *links = nullptr;
   cudaGraph_t graph = nullptr;

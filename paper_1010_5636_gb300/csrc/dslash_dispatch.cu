@@ -41,13 +41,22 @@ cudaError_t launch_q(const Geom& g, const QLaunch& L0, cudaStream_t st) {
   if (L0.nsites <= 0) return cudaSuccess;
   QLaunch L = L0;
   if (L.mode == Q_MRHS && (L.nrhs < 1 || L.reduce)) return cudaErrorInvalidValue;
+  if ((L.mode == Q_BPLAIN || L.mode == Q_BCG) && (L.nrhs < 1 || !L.reduce)) return cudaErrorInvalidValue;
   if (L.split == 0) L.split = default_split(L.prec, L.recon, L.nsites != 2 * g.Vh);
-  if (L.mode == Q_MRHS) L.split = 1;
+  if (L.mode == Q_MRHS || L.mode == Q_BPLAIN || L.mode == Q_BCG) L.split = 1;
   switch (L.prec) {
     case 0: return launch_q_fp64(g, L, st);
     case 1: return launch_q_fp32(g, L, st);
     case 2: return launch_q_fp16(g, L, st);
   }
   return cudaErrorInvalidValue;
+}
+}  // namespace nd
+
+namespace nd {
+int64_t bcg_partials(const Geom& g, int prec, int nsys) {
+  const int sites_per_block = prec == 0 ? 256 : 64;
+  const int64_t nblk = (2 * (int64_t)g.Vh + sites_per_block - 1) / sites_per_block;
+  return nblk * 2 * nsys;
 }
 }  // namespace nd

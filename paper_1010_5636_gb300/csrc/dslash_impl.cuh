@@ -47,21 +47,33 @@ __device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& a
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS = Q_THREADS, int MINB = 1>
 __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A0) {
   using T = typename Traits<P>::real;
-  if (A0.cgs && (A0.cgs[CG_DONE] != 0.0 || A0.cgs[CG_PENDING] != 0.0)) return;
+  // batched modes run one independent system per RHS; BASE is the per-system operation
+  constexpr bool BATCH = MODE == Q_BPLAIN || MODE == Q_BCG;
+  constexpr int BASE = (MODE == Q_MRHS || MODE == Q_BPLAIN) ? Q_PLAIN : (MODE == Q_BCG ? Q_CGUPDATE : MODE);
   constexpr int SITES = THREADS / SPLIT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = SPLIT == 1 ? 0 : warp % SPLIT;
   const int jloc = (warp / SPLIT) * 32 + lane;
-  int blk = blockIdx.x;
+  int blk = blockIdx.x, nblk = gridDim.x;
   QLaunch A = A0;
-  if constexpr (MODE == Q_MRHS) {
+  ReduceSlot slot = A0.slot;
+  if constexpr (MODE == Q_MRHS || BATCH) {
     // several right-hand sides: consecutive blocks take the same sites for successive RHS
     const int r = blk % A.nrhs;
     blk /= A.nrhs;
+    nblk /= A.nrhs;
     A.in = static_cast<const char*>(A.in) + r * A.rhs_stride;
     A.out = static_cast<char*>(A.out) + r * A.rhs_stride;
     if (A.y) A.y = static_cast<const char*>(A.y) + r * A.rhs_stride;
+    if constexpr (BATCH) {
+      A.cgs = A0.cgs + r * A0.cgs_stride;
+      slot.result = A0.slot.result + r * A0.cgs_stride;
+      slot.counter = A0.slot.counter + r;
+      slot.partials = A0.slot.partials + (int64_t)r * nblk * 2;
+    }
   }
+  // every block of one system sees the same flags, so whole reductions are skipped together
+  if (A.cgs && (A.cgs[CG_DONE] != 0.0 || A.cgs[CG_PENDING] != 0.0)) return;
   const int i = blk * SITES + jloc;
   const bool act = i < A.nsites;
   int p = 0, h = 0;
@@ -106,17 +118,17 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
   double red[2] = {0.0, 0.0};
   // in the CG mode the operator scale and the base shift come from the solver state, so one
   // captured launch serves every solve
-  const double a_d = MODE == Q_CGUPDATE ? A.cgs[CG_ASCALE] : A.a;
-  const double b_d = MODE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
+  const double a_d = BASE == Q_CGUPDATE ? A.cgs[CG_ASCALE] : A.a;
+  const double b_d = BASE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
   const T diag = (T)A.diag, ca = (T)a_d, cb = (T)b_d;
   const bool read_diag = REDUCE || A.diag != 0.0;
-  constexpr bool IN_PLACE = MODE == Q_CGUPDATE || MODE == Q_XPAY2;
+  constexpr bool IN_PLACE = BASE == Q_CGUPDATE || BASE == Q_XPAY2;
   Spinor<T> d, y, z;
   if (act) {
     if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
-    if ((MODE != Q_PLAIN && MODE != Q_MRHS) || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
-    if (MODE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
-    if (MODE == Q_XPAY2) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
+    if (BASE != Q_PLAIN || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
+    if (BASE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
+    if (BASE == Q_XPAY2) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
   }
   // in the in-place modes every part must have read its copy of z before any part of the
   // block stores (each site's chunks are written by different warps)
@@ -132,14 +144,14 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
         v = (a < 2 ? ca : -ca) * v;  // gamma5 = diag(1, 1, -1, -1)
         res.s[a][c] = v;
       }
-    if (MODE == Q_PLAIN || MODE == Q_MRHS) {
+    if (BASE == Q_PLAIN) {
       if (A.y) {
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
           for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c];
       }
-    } else if (MODE == Q_XPAY2) {
+    } else if (BASE == Q_XPAY2) {
       const T cc = (T)A.c;
 #pragma unroll
       for (int a = 0; a < 4; ++a)
@@ -168,7 +180,7 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
       red[1] = (double)s1;
     }
   }
-  if (REDUCE) grid_sum<2>(red, A.slot);
+  if (REDUCE) grid_sum<2>(red, slot, nblk, blk);
 }
 
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS, int MINB>
@@ -215,6 +227,14 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
       if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
       return launch_q5<P, R, Q_MRHS, false, 1, 64, 8>(g, L, st);
+    case Q_BPLAIN:
+      if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
+      if (P == P64) return launch_q5<P, R, Q_BPLAIN, true, 1, 256, 1>(g, L, st);
+      return launch_q5<P, R, Q_BPLAIN, true, 1, 64, 8>(g, L, st);
+    case Q_BCG:
+      if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
+      if (P == P64) return launch_q5<P, R, Q_BCG, true, 1, 256, 1>(g, L, st);
+      return launch_q5<P, R, Q_BCG, true, 1, 64, 8>(g, L, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -36,7 +36,10 @@ constexpr int CG_NMAX = 32;
 constexpr int CG_STATE_DOUBLES = CG_NSCALAR + SH_NARRAY * CG_NMAX;
 __host__ __device__ inline int sh(int array, int l) { return CG_NSCALAR + array * CG_NMAX + l; }
 
-enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2, Q_MRHS = 3 };  // Q_MRHS: Q_PLAIN over nrhs fields
+// Q_MRHS: Q_PLAIN over nrhs fields.  Q_BPLAIN / Q_BCG: Q_PLAIN / Q_CGUPDATE with a reduction,
+// over nrhs independent systems (the batched CG): field r at + r * rhs_stride, its scalar block
+// at cgs + r * cgs_stride, its reduction partials / counter / result offset likewise.
+enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2, Q_MRHS = 3, Q_BPLAIN = 4, Q_BCG = 5 };
 
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y      (Q_PLAIN; y may be null)
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y + c * z   (Q_XPAY2; z may alias out)
@@ -64,6 +67,7 @@ struct QLaunch {
                       // per-block scratch for 256 sites per block)
   int nrhs;           // right-hand sides in one launch (0 or 1: one)
   int64_t rhs_stride; // bytes between consecutive RHS fields
+  int64_t cgs_stride; // doubles between consecutive systems' scalar blocks (batched modes)
 };
 int default_split(int prec, int recon, bool half);
 
@@ -107,6 +111,16 @@ cudaError_t blas_lincomb(const Geom& g, void* out, double beta, const void* y, c
 
 // FP64 field of deterministic pseudo-random reals in [-1, 1)
 cudaError_t blas_random(const Geom& g, void* out, uint64_t seed, cudaStream_t st);
+
+// ---------------------------------------------------------------- batched CG (mscg.cu)
+// nsys independent shifted CG systems, each with a full scalar block (CG_STATE_DOUBLES, one
+// shift) at states + s * CG_STATE_DOUBLES; fields at + s * field bytes.
+cudaError_t bcg_init(double* states, int nsys, cudaStream_t st);
+cudaError_t bcg_scalar(double* states, int nsys, int maxit, const cudaGraphConditionalHandle* h, cudaStream_t st);
+cudaError_t bcg_update(const Geom& g, int ps, const void* r, void* p, void* x, size_t fstride, const double* states,
+                       int nsys, cudaStream_t st);
+// Partials needed by one batched reducing Q launch over nsys systems (doubles).
+int64_t bcg_partials(const Geom& g, int prec, int nsys);
 
 // ---------------------------------------------------------------- multi-shift CG (mscg.cu)
 cudaError_t mscg_init(double* state, int n, cudaStream_t st);

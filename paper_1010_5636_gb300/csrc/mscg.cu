@@ -202,3 +202,133 @@ cudaError_t mscg_update(const Geom& g, int ps, int px, bool ymode, const void* r
 }
 
 }  // namespace nd
+
+// ---------------------------------------------------------------- batched CG
+// nsys independent systems (A + sigma_s) x_s = b_s, each with its own scalar block laid out as
+// the multi-shift state with one shift.  The recurrences are those of plain CG (zeta = 1):
+// alpha = (r, r) / (p, (A + sigma) p), beta = (r, r)_new / (r, r).
+
+namespace nd {
+
+__global__ void bcg_init_kernel(double* states, int nsys) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nsys) return;
+  double* st = states + (int64_t)s * CG_STATE_DOUBLES;
+  st[sh(SH_ZETA, 0)] = 1.0;
+  st[sh(SH_ZETAP, 0)] = 1.0;
+  st[sh(SH_ACTIVE, 0)] = 1.0;
+  st[sh(SH_RES, 0)] = 1.0;
+  st[CG_DONE] = 0.0;
+  st[CG_PENDING] = 0.0;
+  st[CG_STATUS] = (double)ND_OK;
+  st[CG_ITER] = 0.0;
+  st[CG_BNORM2] = st[CG_RR];
+  st[CG_SIGMA0] = st[sh(SH_SIGMA, 0)];
+  if (!(st[CG_RR] > 0.0)) {
+    st[CG_PENDING] = 1.0;
+    if (st[CG_RR] != 0.0) {
+      st[CG_DONE] = 1.0;
+      st[CG_STATUS] = (double)ND_ERR_NAN;
+    }
+  }
+}
+
+template <bool GRAPH>
+__global__ void bcg_scalar_kernel(double* states, int nsys, int maxit, cudaGraphConditionalHandle h) {
+  const int s = threadIdx.x;
+  int running = 0;
+  if (s < nsys) {
+    double* st = states + (int64_t)s * CG_STATE_DOUBLES;
+    if (st[CG_DONE] != 0.0 || st[CG_PENDING] != 0.0) {
+      st[CG_DONE] = 1.0;  // its last update has been applied
+    } else {
+      const double rr = st[CG_RR], rrn = st[CG_RRNEW];
+      const double den = st[CG_ASCALE] * st[CG_TT] + st[CG_SIGMA0] * st[CG_PP];
+      const double alpha = rr / den, beta = rrn / rr;
+      st[sh(SH_UPD, 0)] = 1.0;
+      st[sh(SH_COEFX, 0)] = alpha;
+      st[sh(SH_COEFR, 0)] = 1.0;
+      st[sh(SH_COEFP, 0)] = beta;
+      const double res = sqrt(rrn / st[CG_BNORM2]);
+      st[sh(SH_RES, 0)] = res;
+      const double it = st[CG_ITER] + 1.0;
+      st[CG_ITER] = it;
+      st[CG_RR] = rrn;
+      if (!(den > 0.0) || !isfinite(den)) {
+        st[CG_DONE] = 1.0;
+        st[CG_STATUS] = isfinite(den) ? (double)ND_ERR_BREAKDOWN : (double)ND_ERR_NAN;
+      } else if (!isfinite(rrn)) {
+        st[CG_DONE] = 1.0;
+        st[CG_STATUS] = (double)ND_ERR_NAN;
+      } else if (res <= st[sh(SH_TOL, 0)] || rrn == 0.0) {
+        st[CG_PENDING] = 1.0;
+      } else if (it >= (double)maxit) {
+        st[CG_PENDING] = 1.0;
+        st[CG_STATUS] = (double)ND_ERR_NOT_CONVERGED;
+      }
+      running = st[CG_DONE] == 0.0 && st[CG_PENDING] == 0.0;
+    }
+  }
+  running = __syncthreads_or(running);
+  // the while-loop ends after the update kernel of the iteration in which the last system
+  // stopped
+  if (GRAPH && threadIdx.x == 0 && !running) cudaGraphSetConditional(h, 0);
+}
+
+template <int PS>
+__global__ void __launch_bounds__(256) bcg_update_kernel(const Geom g, const char* r, char* p, char* x, size_t fstride,
+                                                         const double* states) {
+  using T = typename Traits<PS>::real;
+  const double* st = states + (int64_t)blockIdx.y * CG_STATE_DOUBLES;
+  if (st[CG_DONE] != 0.0) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * g.Vh) return;
+  const int pp = i >= g.Vh ? 1 : 0, h = i - pp * g.Vh;
+  const size_t off = (size_t)blockIdx.y * fstride;
+  Spinor<T> vr, vp, vx;
+  SpinorIO<PS>::load(vr, r + off, g.Vh, pp, h);
+  SpinorIO<PS>::load(vp, p + off, g.Vh, pp, h);
+  SpinorIO<PS>::load(vx, x + off, g.Vh, pp, h);
+  const T a = (T)st[sh(SH_COEFX, 0)], b = (T)st[sh(SH_COEFP, 0)];
+#pragma unroll
+  for (int s = 0; s < 4; ++s)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      vx.s[s][c] = vx.s[s][c] + a * vp.s[s][c];
+      vp.s[s][c] = vr.s[s][c] + b * vp.s[s][c];
+    }
+  SpinorIO<PS>::store(vx, x + off, g.Vh, pp, h);
+  SpinorIO<PS>::store(vp, p + off, g.Vh, pp, h);
+}
+
+cudaError_t bcg_init(double* states, int nsys, cudaStream_t st) {
+  bcg_init_kernel<<<(nsys + 31) / 32, 32, 0, st>>>(states, nsys);
+  return cudaGetLastError();
+}
+
+cudaError_t bcg_scalar(double* states, int nsys, int maxit, const cudaGraphConditionalHandle* h, cudaStream_t st) {
+  if (nsys > 1024) return cudaErrorInvalidValue;
+  const int threads = ((nsys + 31) / 32) * 32;
+  if (h)
+    bcg_scalar_kernel<true><<<1, threads, 0, st>>>(states, nsys, maxit, *h);
+  else
+    bcg_scalar_kernel<false><<<1, threads, 0, st>>>(states, nsys, maxit, cudaGraphConditionalHandle{});
+  return cudaGetLastError();
+}
+
+cudaError_t bcg_update(const Geom& g, int ps, const void* r, void* p, void* x, size_t fstride, const double* states,
+                       int nsys, cudaStream_t st) {
+  const dim3 grid((2 * g.Vh + 255) / 256, nsys);
+  const char* rr = static_cast<const char*>(r);
+  char* pp = static_cast<char*>(p);
+  char* xx = static_cast<char*>(x);
+  switch (ps) {
+    case P64: bcg_update_kernel<P64><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
+    case P32: bcg_update_kernel<P32><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
+    case P16: bcg_update_kernel<P16><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace nd

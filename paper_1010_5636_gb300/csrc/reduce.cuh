@@ -43,17 +43,19 @@ __device__ __forceinline__ void block_sum(double (&v)[K]) {
   }
 }
 
-// Block reduction + grid-level finish.  Every thread of every block must call it.
+// Block reduction + grid-level finish.  Every thread of every block must call it.  A launch
+// that runs several independent reductions passes each one's block count and this block's
+// index within it (and a slot with its own partials, counter and result).
 template <int K>
-__device__ __forceinline__ void grid_sum(double (&v)[K], const ReduceSlot& slot) {
+__device__ __forceinline__ void grid_sum(double (&v)[K], const ReduceSlot& slot, int nblocks, int bid) {
   block_sum<K>(v);
   __shared__ bool last;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) slot.partials[blockIdx.x * K + k] = v[k];
+    for (int k = 0; k < K; ++k) slot.partials[bid * K + k] = v[k];
     __threadfence();
     unsigned t = atomicAdd(slot.counter, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == (unsigned)nblocks - 1);
   }
   __syncthreads();
   if (!last) return;
@@ -61,7 +63,7 @@ __device__ __forceinline__ void grid_sum(double (&v)[K], const ReduceSlot& slot)
   double s[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) s[k] = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x)
 #pragma unroll
     for (int k = 0; k < K; ++k) s[k] += __ldcg(slot.partials + i * K + k);
   block_sum<K>(s);
@@ -70,6 +72,11 @@ __device__ __forceinline__ void grid_sum(double (&v)[K], const ReduceSlot& slot)
     for (int k = 0; k < K; ++k) slot.result[k] = s[k];
     *slot.counter = 0u;
   }
+}
+
+template <int K>
+__device__ __forceinline__ void grid_sum(double (&v)[K], const ReduceSlot& slot) {
+  grid_sum<K>(v, slot, (int)gridDim.x, (int)blockIdx.x);
 }
 
 }  // namespace nd

@@ -91,8 +91,8 @@ static nd_ms_graph* ms_graph(nd_ctx* c, int ps, int px, bool ymode, void* r, voi
                              void* x_or_y, size_t fx, double* state, int n, int maxit) {
   if (!c->graphs_ok) return nullptr;
   for (auto& gr : c->ms_graphs)
-    if (gr.ps == ps && gr.px == px && gr.ymode == (int)ymode && gr.n == n && gr.maxit == maxit && gr.r == r &&
-        gr.t == t && gr.p == p_all && gr.x == x_or_y && gr.state == state && gr.links == c->links[ps])
+    if (gr.kind == 0 && gr.ps == ps && gr.px == px && gr.ymode == (int)ymode && gr.n == n && gr.maxit == maxit &&
+        gr.r == r && gr.t == t && gr.p == p_all && gr.x == x_or_y && gr.state == state && gr.links == c->links[ps])
       return &gr;
   nd_ms_graph G;
   G.ps = ps, G.px = px, G.ymode = ymode, G.n = n, G.maxit = maxit;
@@ -204,6 +204,161 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
   return ND_OK;
 }
 
+// ------------------------------------------------------------------ batched CG
+// One iteration of nsys independent shifted CG systems (fields at + s * fs) on stream st.
+static cudaError_t bcg_iteration(nd_ctx* c, cudaStream_t st, int ps, char* r, char* t, char* p, char* x, size_t fs,
+                                 double* states, double* partials, unsigned* counters, int nsys, int maxit,
+                                 const cudaGraphConditionalHandle* h) {
+  QLaunch L1{};
+  L1.prec = ps;
+  L1.recon = c->recon[ps];
+  L1.mode = Q_BPLAIN;
+  L1.reduce = true;
+  L1.links = c->links[ps];
+  L1.in = p;
+  L1.out = t;
+  L1.diag = 4.0 + c->m;
+  L1.a = 1.0;
+  L1.nsites = (int)c->V;
+  L1.nrhs = nsys;
+  L1.rhs_stride = (int64_t)fs;
+  L1.cgs = states;
+  L1.cgs_stride = CG_STATE_DOUBLES;
+  L1.slot.partials = partials;
+  L1.slot.counter = counters;
+  L1.slot.result = states + CG_TT;
+  cudaError_t e = launch_q(c->g, L1, st);
+  if (e != cudaSuccess) return e;
+  QLaunch L2 = L1;
+  L2.mode = Q_BCG;
+  L2.in = t;
+  L2.out = r;
+  L2.y = p;
+  L2.slot.result = states + CG_RRNEW;
+  e = launch_q(c->g, L2, st);
+  if (e != cudaSuccess) return e;
+  e = bcg_scalar(states, nsys, maxit, h, st);
+  if (e != cudaSuccess) return e;
+  return bcg_update(c->g, ps, r, p, x, fs, states, nsys, st);
+}
+
+// Solve (ascale Q^2 + sigma_s) x_s = b_s for s < nsys (independent systems run in lockstep: one
+// multi-RHS Q launch per step for all of them).  b, x: nsys consecutive fields of precision ps.
+nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<double>& sigma,
+                  const std::vector<double>& tol, double ascale, int maxit, std::vector<int>* iters) {
+  const int nsys = (int)sigma.size();
+  if (nsys < 1 || nsys > 1024) return fail(c, ND_ERR_INVALID_ARG, "batched CG: 1..1024 systems");
+  if (!c->links[ps]) return fail(c, ND_ERR_STATE, "batched CG: links not set in the Krylov precision");
+  const size_t fs = (size_t)spinor_bytes(ps, c->Vh);
+  char* r = static_cast<char*>(field(c, "bc_r", ps, nsys));
+  char* t = static_cast<char*>(field(c, "bc_t", ps, nsys));
+  char* p = static_cast<char*>(field(c, "bc_p", ps, nsys));
+  double* states = static_cast<double*>(workspace(c, "bc_state", sizeof(double) * CG_STATE_DOUBLES * nsys));
+  double* partials = static_cast<double*>(workspace(c, "bc_partials", sizeof(double) * bcg_partials(c->g, ps, nsys)));
+  unsigned* counters = static_cast<unsigned*>(workspace(c, "bc_counters", sizeof(unsigned) * nsys));
+  if (!r || !t || !p || !states || !partials || !counters) return fail(c, ND_ERR_OOM, "batched CG: workspace");
+  std::vector<double> h((size_t)CG_STATE_DOUBLES * nsys, 0.0);
+  for (int s = 0; s < nsys; ++s) {
+    double* hs = h.data() + (size_t)s * CG_STATE_DOUBLES;
+    hs[sh(SH_SIGMA, 0)] = sigma[s];
+    hs[sh(SH_TOL, 0)] = tol[s];
+    hs[CG_ASCALE] = ascale;
+  }
+  ND_TRY_CUDA(c, cudaMemcpyAsync(states, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream));
+  ND_TRY_CUDA(c, cudaMemsetAsync(counters, 0, sizeof(unsigned) * nsys, c->stream));
+  ND_TRY_CUDA(c, cudaMemcpyAsync(p, b, fs * nsys, cudaMemcpyDeviceToDevice, c->stream));
+  ND_TRY_CUDA(c, cudaMemsetAsync(x, 0, fs * nsys, c->stream));
+  for (int s = 0; s < nsys; ++s)
+    ND_TRY_CUDA(c, blas_axpby(c->g, ps, r + s * fs, 1.0, static_cast<const char*>(b) + s * fs, 0.0, nullptr, true,
+                              slot(c, states + (size_t)s * CG_STATE_DOUBLES + CG_RR), c->stream));
+  ND_TRY_CUDA(c, bcg_init(states, nsys, c->stream));
+  // graph: a device while-loop over the iterations, reused while the buffers are the same
+  nd_ms_graph* G = nullptr;
+  if (c->graphs_ok) {
+    for (auto& gr : c->ms_graphs)
+      if (gr.kind == 1 && gr.ps == ps && gr.n == nsys && gr.maxit == maxit && gr.r == r && gr.t == t && gr.p == p &&
+          gr.x == x && gr.state == states && gr.links == c->links[ps])
+        G = &gr;
+    if (!G) {
+      nd_ms_graph NG;
+      NG.kind = 1, NG.ps = ps, NG.n = nsys, NG.maxit = maxit;
+      NG.r = r, NG.t = t, NG.p = p, NG.x = x, NG.state = states, NG.links = c->links[ps];
+      bool ok = true;
+      cudaGraphConditionalHandle hc{};
+      cudaGraphNode_t node;
+      alignas(cudaGraphNodeParams) unsigned char cp_raw[sizeof(cudaGraphNodeParams)];
+      memset(cp_raw, 0, sizeof(cp_raw));
+      cudaGraphNodeParams& cp = *reinterpret_cast<cudaGraphNodeParams*>(cp_raw);
+      ok = ok && cudaGraphCreate(&NG.graph, 0) == cudaSuccess;
+      ok = ok && cudaGraphConditionalHandleCreate(&hc, NG.graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+      if (ok) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        ok = cudaGraphAddNode(&node, NG.graph, nullptr, nullptr, 0, &cp) == cudaSuccess;
+      }
+      if (ok && !c->cap_stream) ok = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+      if (ok) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        ok = cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+          const cudaError_t e1 =
+              bcg_iteration(c, c->cap_stream, ps, r, t, p, static_cast<char*>(x), fs, states, partials, counters,
+                            nsys, maxit, &hc);
+          const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &body);
+          ok = e1 == cudaSuccess && e2 == cudaSuccess;
+        }
+      }
+      ok = ok && cudaGraphInstantiate(&NG.exec, NG.graph, 0) == cudaSuccess;
+      if (!ok) {
+        cudaGetLastError();
+        if (NG.exec) cudaGraphExecDestroy(NG.exec);
+        if (NG.graph) cudaGraphDestroy(NG.graph);
+        c->graphs_ok = false;
+      } else {
+        if (c->ms_graphs.size() >= 32) {
+          cudaGraphExecDestroy(c->ms_graphs.front().exec);
+          cudaGraphDestroy(c->ms_graphs.front().graph);
+          c->ms_graphs.erase(c->ms_graphs.begin());
+        }
+        c->ms_graphs.push_back(NG);
+        G = &c->ms_graphs.back();
+      }
+    }
+  }
+  std::vector<double> hs((size_t)CG_STATE_DOUBLES * nsys);
+  if (G) {
+    ND_TRY_CUDA(c, cudaGraphLaunch(G->exec, c->stream));
+    ND_TRY(read_back(c, states, hs.data(), (int)hs.size()));
+  } else {
+    int chunk = 8;
+    for (;;) {
+      for (int k = 0; k < chunk; ++k)
+        ND_TRY_CUDA(c, bcg_iteration(c, c->stream, ps, r, t, p, static_cast<char*>(x), fs, states, partials, counters,
+                                     nsys, maxit, nullptr));
+      ND_TRY(read_back(c, states, hs.data(), (int)hs.size()));
+      bool all = true;
+      for (int s = 0; s < nsys; ++s) {
+        const double* q = hs.data() + (size_t)s * CG_STATE_DOUBLES;
+        if (q[CG_DONE] == 0.0 && q[CG_PENDING] == 0.0) all = false;
+      }
+      if (all) break;
+      chunk = std::min(chunk * 2, 64);
+    }
+  }
+  if (iters) iters->assign(nsys, 0);
+  for (int s = 0; s < nsys; ++s) {
+    const double* q = hs.data() + (size_t)s * CG_STATE_DOUBLES;
+    if (iters) (*iters)[s] = (int)q[CG_ITER];
+    const int stt = (int)q[CG_STATUS];
+    if (stt != ND_OK && stt != ND_ERR_NOT_CONVERGED)
+      return fail(c, (nd_status)stt, stt == ND_ERR_BREAKDOWN ? "batched CG: breakdown" : "batched CG: NaN or Inf");
+  }
+  return ND_OK;
+}
+
 nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale, double bnorm2,
                      double* rel) {
   void* t = field(c, "res_t", 0);
@@ -232,11 +387,8 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   if (const char* e = std::getenv("ND_MIXED_FLOOR_IN")) floor_in = std::atof(e);
   void* bS = field(c, "mx_bS", ps);
   char* x32 = static_cast<char*>(field(c, "mx_x32", 1, n));
-  void* x64 = field(c, "mx_x64", 0);
   void* r64 = field(c, "mx_r64", 0);
-  void* r32 = field(c, "mx_r32", 1);
-  void* e32 = field(c, "mx_e32", 1);
-  if (!bS || !x32 || !x64 || !r64 || !r32 || !e32) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
+  if (!bS || !x32 || !r64) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
   ND_TRY_CUDA(c, blas_convert(c->g, ps, bS, 0, b64, c->stream));
   std::vector<double> tol_s(n);
   for (int l = 0; l < n; ++l) tol_s[l] = std::max(tol[l], floor_s);
@@ -246,34 +398,54 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   st->iters = ms.iters;
   st->sloppy_iters = ms.iters;
   st->max_resid = 0.0;
-  const size_t f32 = (size_t)spinor_bytes(1, c->Vh);
-  for (int l = 0; l < n; ++l) {
-    ND_TRY_CUDA(c, blas_convert(c->g, 0, x64, 1, x32 + l * f32, c->stream));
-    double rel = 0.0, first_rel = -1.0;
-    int outer = 0;
-    for (;;) {
-      ND_TRY(residual64(c, r64, b64, x64, sigma[l], ascale, bnorm2, &rel));
-      if (first_rel < 0) first_rel = rel;
-      if (rel <= tol[l]) break;
-      if (outer >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
-      ++outer;
-      // correction e: (A + sigma_l) e = r in FP32, from zero, to a relative reduction that
-      // reaches tol with a margin (or floor_in, whichever is larger)
-      ND_TRY_CUDA(c, blas_convert(c->g, 1, r32, 0, r64, c->stream));
-      const double inner = std::max(0.3 * tol[l] / rel, floor_in);
-      MsResult mi;
-      s = mscg_run(c, 1, 1, false, r32, e32, {sigma[l]}, {inner}, {}, ascale, maxit, &mi);
-      if (s != ND_OK && s != ND_ERR_NOT_CONVERGED) return s;
-      st->sloppy_iters += mi.iters;
-      ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, e32, c->stream));
-      ND_TRY_CUDA(c, blas_axpby(c->g, 0, x64, 1.0, x64, 1.0, r64, false, slot(c, nullptr), c->stream));
+  // FP64 defect correction of every shift, the correction solves of all shifts that still miss
+  // their target batched into one lockstep CG (one multi-RHS Q launch per step)
+  const size_t f32 = (size_t)spinor_bytes(1, c->Vh), f64 = (size_t)spinor_bytes(0, c->Vh);
+  char* X64 = static_cast<char*>(field(c, "mx_X64", 0, n));
+  char* R32 = static_cast<char*>(field(c, "mx_R32", 1, n));
+  char* E32 = static_cast<char*>(field(c, "mx_E32", 1, n));
+  if (!X64 || !R32 || !E32) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
+  for (int l = 0; l < n; ++l) ND_TRY_CUDA(c, blas_convert(c->g, 0, X64 + l * f64, 1, x32 + l * f32, c->stream));
+  std::vector<double> rel(n, 1.0), first(n, -1.0);
+  std::vector<int> outer(n, 0);
+  std::vector<bool> done(n, false);
+  for (int sweep = 0;; ++sweep) {
+    std::vector<int> pend;
+    std::vector<double> sig_p, tol_p;
+    for (int l = 0; l < n; ++l) {
+      if (done[l]) continue;
+      ND_TRY(residual64(c, r64, b64, X64 + l * f64, sigma[l], ascale, bnorm2, &rel[l]));
+      if (first[l] < 0) first[l] = rel[l];
+      if (rel[l] <= tol[l]) {
+        done[l] = true;
+        continue;
+      }
+      ND_TRY_CUDA(c, blas_convert(c->g, 1, R32 + pend.size() * f32, 0, r64, c->stream));
+      pend.push_back(l);
+      sig_p.push_back(sigma[l]);
+      tol_p.push_back(std::max(0.3 * tol[l] / rel[l], floor_in));
     }
+    if (pend.empty()) break;
+    if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
+    std::vector<int> it;
+    s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, maxit, &it);
+    if (s != ND_OK) return s;
+    for (size_t k = 0; k < pend.size(); ++k) {
+      const int l = pend[k];
+      st->sloppy_iters += it[k];
+      ++outer[l];
+      ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, E32 + k * f32, c->stream));
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, 1.0, X64 + l * f64, 1.0, r64, false, slot(c, nullptr),
+                                c->stream));
+    }
+  }
+  for (int l = 0; l < n; ++l) {
     if (std::getenv("ND_TRACE"))
       std::fprintf(stderr, "mixed solve: shift %d sigma %.3e sloppy resid %.3e outer %d final %.3e\n", l, sigma[l],
-                   first_rel, outer, rel);
-    st->outer = std::max(st->outer, outer);
-    st->max_resid = std::max(st->max_resid, rel);
-    ND_TRY(sink(sink_ctx, l, x64));
+                   first[l], outer[l], rel[l]);
+    st->outer = std::max(st->outer, outer[l]);
+    st->max_resid = std::max(st->max_resid, rel[l]);
+    ND_TRY(sink(sink_ctx, l, X64 + l * f64));
   }
   return ND_OK;
 }
