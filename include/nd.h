@@ -226,6 +226,16 @@ nd_status nd_apply_DN(nd_ctx* ctx, double* out_dev, const double* in_dev, const 
 nd_status nd_force(nd_ctx* ctx, double* F_dev, const double* phi_dev, double tol, int maxit, nd_prec inner,
                    nd_solve_info* info);
 
+/* S = phi^dagger (Q^2)^{-1} phi (host, S may be NULL) and its gradient with respect to the link
+ * matrices treated as general complex 3x3 matrices: G_dev [4][V][3][3][2] (device, FP64) is the
+ * conjugate Wirtinger derivative dS/dU^*, so dS = 2 Re sum conj(G_mu(x)_ij) dU_mu(x)_ij
+ * (torch.autograd's gradient of a real loss is 2 G).  Derived from dS = -2 Re Y^dagger dQ X, Y = Q X (Sec. 2.1 definition of Q);
+ * the su(3) projection of the same quantity is nd_force.  X_dev (canonical FP64 spinor, device,
+ * may be NULL) receives X = (Q^2)^{-1} phi, which is also dS/dphi^* in the same convention.
+ * Solve as nd_force. */
+nd_status nd_link_gradient(nd_ctx* ctx, double* G_dev, double* X_dev, double* S, const double* phi_dev, double tol,
+                           int maxit, nd_prec inner, nd_solve_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ _SIGS = {
     "nd_apply_sign": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_apply_DN": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_force": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
+    "nd_link_gradient": ([_P, _P, _P, ctypes.POINTER(_D), _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
 }
 
 _lib = None
@@ -272,6 +273,17 @@ def nd_force(ctx, F, phi, tol=1e-12, maxit=100000, inner=ND_FP64):
     _check(ctx, lib().nd_force(ctx, _ptr(F), _ptr(_f64(phi)), float(tol), int(maxit), int(inner), ctypes.byref(info)),
            "nd_force")
     return info
+
+
+def nd_link_gradient(ctx, G, phi, tol=1e-12, maxit=100000, inner=ND_FP64, X=None):
+    """Returns (S, info); G (complex128 [4, V, 3, 3] on cuda) receives dS/dU*, X (optional) receives
+    (Q^2)^{-1} phi (see include/nd.h)."""
+    info = nd_solve_info()
+    S = ctypes.c_double()
+    _check(ctx, lib().nd_link_gradient(ctx, _ptr(_f64(G)), _ptr(X if X is None else _f64(X)), ctypes.byref(S),
+                                       _ptr(_f64(phi)), float(tol), int(maxit), int(inner), ctypes.byref(info)),
+           "nd_link_gradient")
+    return S.value, info
 
 
 # ------------------------------------------------------------------ convenience object

@@ -106,6 +106,77 @@ __device__ __forceinline__ void force_link(const Geom& g, const Site& s, int p, 
   for (int k = 0; k < 8; ++k) o[k] = -0.5 * f[k];
 }
 
+// Euclidean gradient of S with respect to the complex link matrix (U treated as a general 3x3
+// matrix, U^dagger in the backward hops as its conjugate transpose):
+//   dS = Re sum_{x,mu} tr(dU_mu(x) K_mu(x)),  K = M1 + M2^dagger,
+//   M1 = sum_alpha [(1 - gamma_mu) X(x+mu)]_alpha [gamma5 Y(x)]_alpha^dagger,
+//   M2 = sum_alpha [(1 + gamma_mu) X(x)]_alpha [gamma5 Y(x+mu)]_alpha^dagger,
+// (from dS = -2 Re Y^dagger dQ X, dQ = -1/2 gamma5 dH).  Stored as G = K^dagger / 2 = dS/dU^*,
+// the conjugate Wirtinger derivative: dS = 2 Re sum conj(G_ij) dU_ij.
+template <int MU>
+__device__ __forceinline__ void gradient_link(const Geom& g, const Site& s, int p, int h, const void* X, const void* Y,
+                                              double* G) {
+  using T = double;
+  bool crossed;
+  const int hf = neighbour_h<MU, true>(g, s, &crossed);
+  const T sgn = (g.apbc && crossed) ? -1.0 : 1.0;
+  Spinor<T> xf, xx, yx, yf;
+  SpinorIO<P64>::load(xf, X, g.Vh, 1 - p, hf);
+  SpinorIO<P64>::load(xx, X, g.Vh, p, h);
+  SpinorIO<P64>::load(yx, Y, g.Vh, p, h);
+  SpinorIO<P64>::load(yf, Y, g.Vh, 1 - p, hf);
+  cx<T> hs[2][3];
+  Spinor<T> a, cc;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      a.s[k][i] = mk(0.0, 0.0);
+      cc.s[k][i] = mk(0.0, 0.0);
+    }
+  spin_project<MU, true>(xf, hs);
+  spin_accumulate<MU, true>(a, hs);
+  spin_project<MU, false>(xx, hs);
+  spin_accumulate<MU, false>(cc, hs);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    yx.s[2][i] = -yx.s[2][i];
+    yx.s[3][i] = -yx.s[3][i];
+    yf.s[2][i] = -yf.s[2][i];
+    yf.s[3][i] = -yf.s[3][i];
+  }
+  double* o = G + ((int64_t)MU * 2 * g.Vh + s.lex) * 18;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // K_ij = (M1)_ij + conj((M2)_ji);  G_ij = conj(K_ji) / 2
+      //      => G_ij = (conj(M1_ji) + M2_ij) / 2
+      cx<T> m1ji = mk(0.0, 0.0), m2ij = mk(0.0, 0.0);
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        cfmac(m1ji, yx.s[al][i], a.s[al][j]);   // a_j conj(g5Y(x)_i)
+        cfmac(m2ij, yf.s[al][j], cc.s[al][i]);  // c_i conj(g5Y(x+mu)_j)
+      }
+      o[2 * (3 * i + j)] = 0.5 * sgn * (m1ji.re + m2ij.re);
+      o[2 * (3 * i + j) + 1] = 0.5 * sgn * (-m1ji.im + m2ij.im);
+    }
+}
+
+__global__ void __launch_bounds__(128) gradient_kernel(const Geom g, const void* X, const void* Y, double* G) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * g.Vh * 4) return;
+  const int mu = i & 3, site = i >> 2;
+  const int p = site & 1, h = site >> 1;
+  const Site s = site_of(g, p, h);
+  switch (mu) {
+    case 0: gradient_link<0>(g, s, p, h, X, Y, G); break;
+    case 1: gradient_link<1>(g, s, p, h, X, Y, G); break;
+    case 2: gradient_link<2>(g, s, p, h, X, Y, G); break;
+    case 3: gradient_link<3>(g, s, p, h, X, Y, G); break;
+  }
+}
+
 __global__ void __launch_bounds__(128) force_kernel(const Geom g, const char* links, const void* X, const void* Y,
                                                     double* F) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,24 +196,26 @@ __global__ void __launch_bounds__(128) force_kernel(const Geom g, const char* li
 
 using namespace nd;
 
-extern "C" nd_status nd_force(nd_ctx* c, double* F, const double* phi, double tol, int maxit, nd_prec inner,
-                              nd_solve_info* info) {
+// X = (Q^2)^{-1} phi (FP64 or mixed), Y = Q X, and S = Re phi^dagger X; fields in the context's
+// workspaces "fo_X", "fo_Y".
+static nd_status solve_action(nd_ctx* c, const double* phi, double tol, int maxit, nd_prec inner, void** Xo, void** Yo,
+                              double* S, nd_solve_info* info) {
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
-  if (!F || !phi || !(tol > 0) || maxit < 1 || inner < ND_FP64 || inner > ND_FP16)
-    return fail(c, ND_ERR_INVALID_ARG, "nd_force: bad argument");
+  if (!phi || !(tol > 0) || maxit < 1 || inner < ND_FP64 || inner > ND_FP16)
+    return fail(c, ND_ERR_INVALID_ARG, "force: bad argument");
   if (c->recon[0] != 18 || !c->links[inner] || (inner != ND_FP64 && !c->links[1]))
-    return fail(c, ND_ERR_STATE, "nd_force: needs FP64 links with 18 reals (and the inner precision)");
+    return fail(c, ND_ERR_STATE, "force: needs FP64 links with 18 reals (and the inner precision)");
   auto t0 = std::chrono::steady_clock::now();
   void* b64 = field(c, "fo_b", 0);
   void* X = field(c, "fo_X", 0);
   void* Y = field(c, "fo_Y", 0);
-  if (!b64 || !X || !Y) return fail(c, ND_ERR_OOM, "nd_force: workspace");
+  if (!b64 || !X || !Y) return fail(c, ND_ERR_OOM, "force: workspace");
   ND_TRY(nd_pack_spinor(c, b64, phi, ND_FP64, 1));
   double bn2;
   ND_TRY_CUDA(c, blas_axpby(c->g, 0, b64, 1.0, b64, 0.0, nullptr, true, slot(c, c->red_scratch), c->stream));
   ND_TRY(read_back(c, c->red_scratch, &bn2, 1));
-  if (!std::isfinite(bn2)) return fail(c, ND_ERR_NAN, "nd_force: source has NaN or Inf");
+  if (!std::isfinite(bn2)) return fail(c, ND_ERR_NAN, "force: source has NaN or Inf");
   nd_solve_info inf{};
   if (bn2 == 0.0) {
     ND_TRY_CUDA(c, cudaMemsetAsync(X, 0, (size_t)spinor_bytes(0, c->Vh), c->stream));
@@ -166,11 +239,40 @@ extern "C" nd_status nd_force(nd_ctx* c, double* F, const double* phi, double to
     inf.max_resid = ms.max_resid;
   }
   ND_TRY(q_apply(c, 0, Y, X));
+  if (S) {
+    ND_TRY_CUDA(c, blas_dot(c->g, 0, b64, X, slot(c, c->red_scratch), c->stream));
+    double d[3];
+    ND_TRY(read_back(c, c->red_scratch, d, 3));
+    *S = d[0];
+  }
+  inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (info) *info = inf;
+  *Xo = X;
+  *Yo = Y;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_force(nd_ctx* c, double* F, const double* phi, double tol, int maxit, nd_prec inner,
+                              nd_solve_info* info) {
+  if (c && !F) return fail(c, ND_ERR_INVALID_ARG, "nd_force: null output");
+  void *X, *Y;
+  ND_TRY(solve_action(c, phi, tol, maxit, inner, &X, &Y, nullptr, info));
   const int n = (int)(4 * c->V);
   force_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->g, static_cast<const char*>(c->links[0]), X, Y, F);
   ND_TRY_CUDA(c, cudaGetLastError());
   ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
-  inf.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  if (info) *info = inf;
+  return ND_OK;
+}
+
+extern "C" nd_status nd_link_gradient(nd_ctx* c, double* G, double* Xout, double* S, const double* phi, double tol,
+                                      int maxit, nd_prec inner, nd_solve_info* info) {
+  if (c && !G) return fail(c, ND_ERR_INVALID_ARG, "nd_link_gradient: null output");
+  void *X, *Y;
+  ND_TRY(solve_action(c, phi, tol, maxit, inner, &X, &Y, S, info));
+  if (Xout) ND_TRY(nd_unpack_spinor(c, Xout, X, ND_FP64, 1));
+  const int n = (int)(4 * c->V);
+  gradient_kernel<<<(n + 127) / 128, 128, 0, c->stream>>>(c->g, X, Y, G);
+  ND_TRY_CUDA(c, cudaGetLastError());
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
   return ND_OK;
 }
