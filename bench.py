@@ -412,6 +412,108 @@ def profile_case(nd, torch, case):
     print(json.dumps({"case": case, "ok": True}))
 
 
+def mrhs_phase(nd, torch):
+    """Multi-RHS Q: 12 point sources (spin x colour) on 24^3x48 in one launch against 12 single
+    launches, and one persistent launch over 8^4, 12^4 and 16^3x32 lattices with 4, 8 and 16
+    RHS against per-lattice launches.  FP32 storage, 12-real links, Haar links (seed 0)."""
+    import numpy as np
+
+    import synth
+
+    def timed(f, reps=10):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            f()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)) * 1e-3
+
+    out = {}
+    dims = (48, 24, 24, 24)
+    V = int(np.prod(dims))
+    ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, torch.from_numpy(synth.gauge_field(dims, "haar", seed=0)).cuda(), (0, RECON, 0))
+    src = torch.zeros((12, V, 4, 3), dtype=torch.complex128, device="cuda")
+    for s in range(4):
+        for c in range(3):
+            src[3 * s + c, 0, s, c] = 1.0
+    sb = nd.nd_spinor_bytes(ctx, 1)
+    a = torch.empty(12 * sb, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    nd.nd_pack_spinor(ctx, a, src, 1, 12)
+    t12 = timed(lambda: nd.nd_apply_Q(ctx, b, a, 1, 12))
+    t1 = timed(lambda: [nd.nd_apply_Q(ctx, b[r * sb:(r + 1) * sb], a[r * sb:(r + 1) * sb], 1, 1) for r in range(12)])
+    link_b = V * 4 * RECON * 4
+    out["point_sources_24c48"] = {
+        "nrhs": 12, "us_one_launch": round(t12 * 1e6, 1), "us_12_launches": round(t1 * 1e6, 1),
+        "site_rhs_per_s": round(12 * V / t12 / 1e9, 3), "unit": "G site*rhs/s",
+        "GB_per_s_links_once": round((link_b + 12 * V * 192) / t12 / 1e9, 1), "speedup": round(t1 / t12, 3)}
+    nd.nd_destroy(ctx)
+    shapes = [((8, 8, 8, 8), 4), ((12, 12, 12, 12), 8), ((32, 16, 16, 16), 16)]
+    ctxs, ins, outs = [], [], []
+    for k, (d, nr) in enumerate(shapes):
+        c = nd.nd_create(d, m=-1.4, s=0.4)
+        nd.nd_set_links(c, torch.from_numpy(synth.gauge_field(d, "haar", seed=0)).cuda(), (0, RECON, 0))
+        ps = torch.from_numpy(synth.spinor(d, seed=2, nrhs=nr)).cuda()
+        x = torch.empty(nd.nd_spinor_bytes(c, 1) * nr, dtype=torch.uint8, device="cuda")
+        nd.nd_pack_spinor(c, x, ps, 1, nr)
+        ctxs.append(c)
+        ins.append(x)
+        outs.append(torch.empty_like(x))
+    nrs = [s[1] for s in shapes]
+    work = sum(int(np.prod(d)) * nr for d, nr in shapes)
+    tb = timed(lambda: nd.nd_apply_Q_batched(ctxs, outs, ins, nrs, 1))
+    ts = timed(lambda: [nd.nd_apply_Q(c, o, i, 1, nr) for c, o, i, nr in zip(ctxs, outs, ins, nrs)])
+    out["mixed_lattices"] = {"lattices": ["8^4 x4", "12^4 x8", "16^3x32 x16"], "us_persistent": round(tb * 1e6, 1),
+                             "us_per_lattice_launches": round(ts * 1e6, 1),
+                             "site_rhs_per_s": round(work / tb / 1e9, 3), "unit": "G site*rhs/s",
+                             "speedup": round(ts / tb, 3)}
+    for c in ctxs:
+        nd.nd_destroy(c)
+    return out
+
+
+def force_phase(nd, torch, reps=2):
+    """Gradient of S = phi^dag (Q^2)^-1 phi on 16^4 near-identity links: FP64 against FP32 inner /
+    FP64 outer, time per gradient (one solve + one link pass), the same 1e-10 relative residual."""
+    import numpy as np
+
+    import synth
+    dims = (16, 16, 16, 16)
+    V = int(np.prod(dims))
+    ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda(),
+                    (18, 12, 12))
+    phi = torch.from_numpy(synth.spinor(dims, seed=1)).cuda()
+    F = torch.empty((4, V, 8), dtype=torch.float64, device="cuda")
+    res = {"workload": "force of phi^dag (Q^2)^-1 phi on 16^4, near-identity links eps=0.3, residual 1e-10"}
+    outs = {}
+    for name, inner in (("fp64", 0), ("mixed_fp32", 1)):
+        nd.nd_force(ctx, F, phi, 1e-10, 100000, inner)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = nd.nd_force(ctx, F, phi, 1e-10, 100000, inner)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        outs[name] = F.clone()
+        res[name] = {"s_per_gradient": round(float(np.median(ts)), 4), "cg_iters": info.iters,
+                     "sloppy_iters": info.sloppy_iters, "resid": info.max_resid}
+    res["mixed_fp32"]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs["mixed_fp32"] - outs["fp64"]) /
+                                                  torch.linalg.vector_norm(outs["fp64"]))
+    res["mixed_fp32"]["speedup_vs_fp64"] = round(res["fp64"]["s_per_gradient"] / res["mixed_fp32"]["s_per_gradient"], 3)
+    nd.nd_destroy(ctx)
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -420,6 +522,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-dn", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS and force measurements")
     ap.add_argument("--dn-reps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None, help="run a small profiling case and exit (hop24)")
@@ -474,6 +577,9 @@ def main():
         line["sweep"] = sweep_phase(nd, torch)
     if not args.no_dn:
         line["dn"] = dn_phase(nd, torch, args.dn_reps)
+    if not args.no_extra:
+        line["multi_rhs"] = mrhs_phase(nd, torch)
+        line["force"] = force_phase(nd, torch)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = oracle_baseline(args.cpu_seconds)
     if rank == 0:

@@ -113,6 +113,15 @@ nd_status nd_apply_Q(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec pre
 nd_status nd_apply_Q_parity(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec, int parity,
                             double diag_coef);
 
+/* Q on several lattices of different sizes in one persistent launch: for k < nlat (<= 32),
+ * out_dev[k] = Q in_dev[k] on nrhs[k] consecutive internal fields of precision prec of the
+ * lattice of ctxs[k] (every context must hold links in prec with the same link form).  Tiles of
+ * 64 sites x one RHS are walked lattice by lattice with the RHS fastest, so each lattice's links
+ * are read from DRAM once for all its RHS.  Runs on `stream` (a cudaStream_t).  Errors are
+ * reported on ctxs[0]. */
+nd_status nd_apply_Q_batched(nd_ctx* const* ctxs, int nlat, void* const* out_dev, const void* const* in_dev,
+                             const int* nrhs, nd_prec prec, void* stream);
+
 /* Convenience: Q on canonical FP64 device spinors (packs, applies in FP64, unpacks). */
 nd_status nd_apply_Q_canonical(nd_ctx* ctx, double* out_dev, const double* in_dev);
 

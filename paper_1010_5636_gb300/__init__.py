@@ -66,6 +66,7 @@ _SIGS = {
     "nd_apply_Q": ([_P, _P, _P, _I, _I], _I),
     "nd_apply_Q_parity": ([_P, _P, _P, _I, _I, _D], _I),
     "nd_apply_Q_canonical": ([_P, _P, _P], _I),
+    "nd_apply_Q_batched": ([_P, _I, _P, _P, _P, _I, _P], _I),
     "nd_apply_Q_norms_static": ([_P, _P, _P, _I, _P], _I),
     "nd_solve": ([_P, _P, _P, _P, _I, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_lowmodes": ([_P, _I, _D, _I, _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
@@ -182,6 +183,18 @@ def nd_apply_Q(ctx, out, inp, prec, nrhs=1):
 def nd_apply_Q_parity(ctx, out, inp, prec, parity, diag_coef):
     _check(ctx, lib().nd_apply_Q_parity(ctx, _ptr(out), _ptr(inp), int(prec), int(parity), float(diag_coef)),
            "nd_apply_Q_parity")
+
+
+def nd_apply_Q_batched(ctxs, outs, ins, nrhs, prec, stream=None):
+    """Q on several lattices (contexts) in one persistent launch; outs/ins: internal-layout tensors."""
+    n = len(ctxs)
+    cs = (ctypes.c_void_p * n)(*[c.value for c in ctxs])
+    op = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    ip = (ctypes.c_void_p * n)(*[t.data_ptr() for t in ins])
+    nr = (ctypes.c_int * n)(*[int(x) for x in nrhs])
+    st = lib().nd_apply_Q_batched(ctypes.cast(cs, _P), n, ctypes.cast(op, _P), ctypes.cast(ip, _P),
+                                  ctypes.cast(nr, _P), int(prec), stream if stream is not None else _stream())
+    _check(ctxs[0], st, "nd_apply_Q_batched")
 
 
 def nd_apply_Q_canonical(ctx, out, inp):

@@ -1,6 +1,8 @@
 // C-ABI entry points of libnd: context lifecycle, field packing, site tables and Q.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <vector>
 
 #include "ctx.h"
 
@@ -244,10 +246,14 @@ nd_status nd_apply_Q(nd_ctx* c, void* out, const void* in, nd_prec prec, int nrh
   L.b = 0.0;
   L.parity0 = 0;
   L.nsites = (int)c->V;
-  if (nrhs == 1)
-    ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
-  else
-    ND_TRY_CUDA(c, launch_q_mrhs(c->g, L, nrhs, sb, c->stream));  // links read once for all RHS
+  if (nrhs > 1) {  // one launch for all RHS, links read once
+    L.mode = Q_MRHS;
+    L.nrhs = nrhs;
+    L.rhs_stride = (int64_t)sb;
+    L.split = 1;
+  }
+  ND_TRY_CUDA(c, autotune_launch(c->g, L, c->stream));
+  ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
   return ND_OK;
 }
 
@@ -268,7 +274,50 @@ nd_status nd_apply_Q_parity(nd_ctx* c, void* out, const void* in, nd_prec prec, 
   L.a = 1.0;
   L.parity0 = parity;
   L.nsites = (int)c->Vh;
+  ND_TRY_CUDA(c, autotune_launch(c->g, L, c->stream));
   ND_TRY_CUDA(c, launch_q(c->g, L, c->stream));
+  return ND_OK;
+}
+
+nd_status nd_apply_Q_batched(nd_ctx* const* ctxs, int nlat, void* const* out, const void* const* in, const int* nrhs,
+                             nd_prec prec, void* stream) {
+  if (!ctxs || nlat < 1 || nlat > ND_MAX_BATCH || !out || !in || !nrhs || prec < ND_FP64 || prec > ND_FP16)
+    return ND_ERR_INVALID_ARG;
+  nd_ctx* c0 = ctxs[0];
+  ND_TRY(check_ctx(c0));
+  std::vector<LatticeWork> w(nlat);
+  int total = 0;
+  for (int k = 0; k < nlat; ++k) {
+    nd_ctx* c = ctxs[k];
+    ND_TRY(check_ctx(c));
+    if (!out[k] || !in[k] || nrhs[k] < 1) return fail(c0, ND_ERR_INVALID_ARG, "nd_apply_Q_batched: bad field");
+    if (!c->links[prec] || c->recon[prec] != c0->recon[prec])
+      return fail(c0, ND_ERR_STATE, "nd_apply_Q_batched: every lattice needs links in prec with the same form");
+    const size_t sb = nd_spinor_bytes(c, prec);
+    const char* ib = static_cast<const char*>(in[k]);
+    const char* ob = static_cast<const char*>(out[k]);
+    if (ib < ob + nrhs[k] * sb && ob < ib + nrhs[k] * sb)
+      return fail(c0, ND_ERR_INVALID_ARG, "nd_apply_Q_batched: out and in must not overlap");
+    w[k].g = c->g;
+    w[k].links = static_cast<const char*>(c->links[prec]);
+    w[k].in = in[k];
+    w[k].out = out[k];
+    w[k].stride = (int64_t)sb;
+    w[k].nrhs = nrhs[k];
+    w[k].tile_begin = total;
+    w[k].diag = 4.0 + c->m;
+    const int64_t tiles = (int64_t)batched_tiles(c->V) * nrhs[k];
+    if (total + tiles > (int64_t)1 << 30) return fail(c0, ND_ERR_INVALID_ARG, "nd_apply_Q_batched: too much work");
+    total += (int)tiles;
+  }
+  LatticeWork* wd = static_cast<LatticeWork*>(workspace(c0, "batched_work", sizeof(LatticeWork) * nlat));
+  if (!wd) return fail(c0, ND_ERR_OOM, "nd_apply_Q_batched: workspace");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ND_TRY_CUDA(c0, cudaMemcpyAsync(wd, w.data(), sizeof(LatticeWork) * nlat, cudaMemcpyHostToDevice, st));
+  int sms = 0;
+  ND_TRY_CUDA(c0, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c0->device));
+  const int grid = std::min(total, sms * 8);
+  ND_TRY_CUDA(c0, launch_q_batched((int)prec, c0->recon[prec], wd, nlat, total, grid, st));
   return ND_OK;
 }
 

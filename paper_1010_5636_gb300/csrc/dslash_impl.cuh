@@ -225,7 +225,7 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
       return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
     case Q_MRHS:
       if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
-      if (P == P64) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
+      if (P == P64 || L.threads == 256) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
       return launch_q5<P, R, Q_MRHS, false, 1, 64, 8>(g, L, st);
     case Q_BPLAIN:
       if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;

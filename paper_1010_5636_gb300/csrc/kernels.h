@@ -78,6 +78,29 @@ cudaError_t launch_q(const Geom& g, const QLaunch& L, cudaStream_t st);
 // site).
 cudaError_t launch_q_mrhs(const Geom& g, const QLaunch& L, int nrhs, size_t stride, cudaStream_t st);
 
+// Several lattices in one persistent launch (dslash_batched.cu): lattice k applies Q to nrhs
+// fields at in + r * stride; its tiles (64 sites of one RHS) start at tile_begin in the list.
+constexpr int ND_MAX_BATCH = 32;
+struct LatticeWork {
+  Geom g;
+  const char* links;
+  const void* in;
+  void* out;
+  int64_t stride;
+  int nrhs;
+  int tile_begin;
+  double diag;
+};
+int batched_tiles(int64_t V);
+cudaError_t launch_q_batched(int prec, int recon, const LatticeWork* work_dev, int nlat, int total, int grid,
+                             cudaStream_t st);
+
+// Launch-shape autotuner (tune.cu): on the first launch of a (precision, links, lattice, kind)
+// the candidates are timed on the caller's stream and the fastest is kept (in memory and, with
+// ND_AUTOTUNE_CACHE=<file>, on disk).  Applies only to launches that may be repeated (out does
+// not alias in); skipped while the stream is being captured or when ND_AUTOTUNE=0.
+cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st);
+
 // Pack / unpack between canonical FP64 ([lex][4][3][2]) and internal precision `prec`.
 cudaError_t launch_pack_spinor(const Geom& g, int prec, void* internal, const double* canon, cudaStream_t st);
 cudaError_t launch_unpack_spinor(const Geom& g, int prec, double* canon, const void* internal, cudaStream_t st);

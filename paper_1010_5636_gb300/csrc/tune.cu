@@ -1,0 +1,122 @@
+// Launch-shape autotuner for the repeatable Q launches (plain Q, one-parity blocks, several
+// right-hand sides).  Candidates: one warp per site in 64-thread (8 per SM) or 256-thread
+// blocks, and two or four warps per site (single RHS only).  Each candidate runs three times
+// on the caller's stream (the output is the same every time, and out never aliases in for
+// these launches); the fastest median wins.  Choices live in memory for the process and, if
+// ND_AUTOTUNE_CACHE names a file, are read from and appended to it (one "key split threads"
+// line each).  ND_AUTOTUNE=0 turns tuning off (defaults: one warp per site, 64 threads).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace nd {
+
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<int, int>> g_tuned;
+bool g_loaded = false;
+
+std::string tune_key(const Geom& g, const QLaunch& L) {
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "q:p%d:r%d:L%dx%dx%dx%d:n%d:m%d:k%d:d%d", L.prec, L.recon, g.L[0], g.L[1], g.L[2],
+                g.L[3], L.nsites, L.mode, L.nrhs > 1 ? L.nrhs : 1, L.diag != 0.0 ? 1 : 0);
+  return buf;
+}
+
+void load_cache() {
+  if (g_loaded) return;
+  g_loaded = true;
+  const char* path = std::getenv("ND_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return;
+  char key[160];
+  int split, threads;
+  while (std::fscanf(f, "%159s %d %d", key, &split, &threads) == 3) g_tuned[key] = {split, threads};
+  std::fclose(f);
+}
+
+void store_cache(const std::string& key, int split, int threads) {
+  const char* path = std::getenv("ND_AUTOTUNE_CACHE");
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d\n", key.c_str(), split, threads);
+  std::fclose(f);
+}
+}  // namespace
+
+cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st) {
+  const char* on = std::getenv("ND_AUTOTUNE");
+  if (on && on[0] == '0') return cudaSuccess;
+  if (L.reduce || (L.mode != Q_PLAIN && L.mode != Q_MRHS) || L.z) return cudaSuccess;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  const std::string key = tune_key(g, L);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    load_cache();
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      L.split = it->second.first;
+      L.threads = it->second.second;
+      return cudaSuccess;
+    }
+  }
+  std::vector<std::pair<int, int>> cand = {{1, 0}, {1, 256}};
+  if (L.mode == Q_PLAIN && L.prec != 0) {
+    cand.push_back({2, 0});
+    cand.push_back({4, 0});
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaGetLastError();
+  float best = 1e30f;
+  std::pair<int, int> pick = cand[0];
+  for (const auto& c : cand) {
+    QLaunch T = L;
+    T.split = c.first;
+    T.threads = c.second;
+    std::vector<float> ts;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      cudaError_t e = launch_q(g, T, st);
+      cudaEventRecord(e1, st);
+      if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return e != cudaSuccess ? e : cudaGetLastError();
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ts.push_back(ms);
+    }
+    std::sort(ts.begin(), ts.end());
+    if (ts[1] < best) {
+      best = ts[1];
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    if (!g_tuned.count(key)) {
+      g_tuned[key] = pick;
+      store_cache(key, pick.first, pick.second);
+    }
+  }
+  L.split = pick.first;
+  L.threads = pick.second;
+  return cudaSuccess;
+}
+
+}  // namespace nd

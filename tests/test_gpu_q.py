@@ -192,7 +192,9 @@ def test_Q_multi_rhs(nd, prec, recon, nrhs):
         nd.nd_unpack_spinor(ctx, got, outb, prec, nrhs)
         nd.nd_unpack_spinor(ctx, ref, one, prec, nrhs)
         torch.cuda.synchronize()
-        assert rel(host(got), host(ref)) <= (1e-15 if prec == 0 else 1e-6)
+        # the autotuner may give the single launches another work split (another summation
+        # order): two valid results agree to the precision's rounding, FP16 storage to ~1e-3
+        assert rel(host(got), host(ref)) <= {0: 1e-15, 1: 1e-6, 2: 2e-3}[prec]
         exp = wilson.apply_Q(U, psi, dims, M)
         assert rel(host(got), exp) <= TOL[prec]
     finally:
@@ -212,3 +214,61 @@ def test_Q_multi_rhs_overlap_rejected(nd):
         assert e.value.status == nd.ND_ERR_INVALID_ARG
     finally:
         nd.nd_destroy(ctx)
+
+
+@pytest.mark.parametrize("prec,recon", [(1, 12), (0, 18), (2, 18)])
+def test_Q_batched_lattices(nd, prec, recon):
+    """One persistent launch over lattices of different sizes and RHS counts equals per-lattice Q."""
+    import torch
+    shapes = [((4, 4, 4, 4), 2), ((6, 4, 4, 6), 3), ((4, 6, 2, 8), 5)]
+    ctxs, ins, outs, refs, canon = [], [], [], [], []
+    try:
+        for k, (dims, nr) in enumerate(shapes):
+            U = synth.gauge_field(dims, "haar", seed=10 + k)
+            ctx = nd.nd_create(dims, m=M)
+            rc = [0, 0, 0]
+            rc[prec] = recon
+            nd.nd_set_links(ctx, dev(U), rc)
+            psi = synth.spinor(dims, seed=20 + k, nrhs=nr)
+            sb = nd.nd_spinor_bytes(ctx, prec)
+            a = torch.empty(sb * nr, dtype=torch.uint8, device="cuda")
+            nd.nd_pack_spinor(ctx, a, dev(psi), prec, nr)
+            ref = torch.empty_like(a)
+            nd.nd_apply_Q(ctx, ref, a, prec, nr)
+            ctxs.append(ctx)
+            ins.append(a)
+            outs.append(torch.empty_like(a))
+            refs.append(ref)
+            canon.append((U, psi, dims, nr))
+        nd.nd_apply_Q_batched(ctxs, outs, ins, [s[1] for s in shapes], prec)
+        for ctx, o, r, (U, psi, dims, nr) in zip(ctxs, outs, refs, canon):
+            V = int(np.prod(dims))
+            got = torch.empty((nr, V, 4, 3), dtype=torch.complex128, device="cuda")
+            exp = torch.empty_like(got)
+            nd.nd_unpack_spinor(ctx, got, o, prec, nr)
+            nd.nd_unpack_spinor(ctx, exp, r, prec, nr)
+            torch.cuda.synchronize()
+            assert rel(host(got), host(exp)) <= {0: 1e-15, 1: 1e-6, 2: 2e-3}[prec]
+            assert rel(host(got), wilson.apply_Q(U, psi, dims, M)) <= TOL[prec]
+    finally:
+        for c in ctxs:
+            nd.nd_destroy(c)
+
+
+def test_autotune_cache_file(nd, tmp_path):
+    """The autotuner writes its choices to ND_AUTOTUNE_CACHE in a fresh process and reuses them."""
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    code = ("import sys; sys.path.insert(0, %r); import torch, synth, paper_1010_5636_gb300 as nd; "
+            "from tests.gpu_util import dev; d=(8,8,8,8); c=nd.nd_create(d); "
+            "nd.nd_set_links(c, dev(synth.gauge_field(d,'haar',seed=0)), (0,12,0)); "
+            "a=torch.zeros(nd.nd_spinor_bytes(c,1), dtype=torch.uint8, device='cuda'); b=torch.empty_like(a); "
+            "nd.nd_apply_Q(c,b,a,1); nd.nd_apply_Q_parity(c,b,a,1,0,0.0); torch.cuda.synchronize()") % os.getcwd()
+    env = dict(os.environ, ND_AUTOTUNE_CACHE=str(cache))
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=os.getcwd())
+    lines = cache.read_text().split("\n")
+    assert len([ln for ln in lines if ln.startswith("q:")]) == 2
+    subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=os.getcwd())
+    assert len([ln for ln in cache.read_text().split("\n") if ln.startswith("q:")]) == 2  # reused, not retuned
