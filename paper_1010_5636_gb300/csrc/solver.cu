@@ -392,9 +392,20 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   ND_TRY_CUDA(c, blas_convert(c->g, ps, bS, 0, b64, c->stream));
   std::vector<double> tol_s(n);
   for (int l = 0; l < n; ++l) tol_s[l] = std::max(tol[l], floor_s);
+  const bool trace = std::getenv("ND_TRACE") != nullptr;
+  auto now = [&]() {
+    if (trace) cudaStreamSynchronize(c->stream);
+    return std::chrono::steady_clock::now();
+  };
+  auto ms_since = [](std::chrono::steady_clock::time_point t) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
+  };
+  double t_res = 0.0, t_bcg = 0.0, t_upd = 0.0;
+  auto t0 = now();
   MsResult ms;
   nd_status s = mscg_run(c, ps, 1, false, bS, x32, sigma, tol_s, {}, ascale, maxit, &ms);
   if (s != ND_OK) return s;
+  if (trace) std::fprintf(stderr, "mixed solve: sloppy multi-shift %d iterations %.2f ms\n", ms.iters, ms_since(t0));
   st->iters = ms.iters;
   st->sloppy_iters = ms.iters;
   st->max_resid = 0.0;
@@ -414,7 +425,9 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
     std::vector<double> sig_p, tol_p;
     for (int l = 0; l < n; ++l) {
       if (done[l]) continue;
+      auto tr = now();
       ND_TRY(residual64(c, r64, b64, X64 + l * f64, sigma[l], ascale, bnorm2, &rel[l]));
+      if (trace) t_res += ms_since(tr);
       if (first[l] < 0) first[l] = rel[l];
       if (rel[l] <= tol[l]) {
         done[l] = true;
@@ -428,8 +441,16 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
     if (pend.empty()) break;
     if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
     std::vector<int> it;
+    auto tb = now();
     s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, maxit, &it);
     if (s != ND_OK) return s;
+    if (trace) {
+      const double dt = ms_since(tb);
+      t_bcg += dt;
+      std::fprintf(stderr, "mixed solve: sweep %d, %zu systems, batched CG max %d iterations %.2f ms\n", sweep,
+                   pend.size(), *std::max_element(it.begin(), it.end()), dt);
+    }
+    auto tu = now();
     for (size_t k = 0; k < pend.size(); ++k) {
       const int l = pend[k];
       st->sloppy_iters += it[k];
@@ -438,7 +459,11 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
       ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, 1.0, X64 + l * f64, 1.0, r64, false, slot(c, nullptr),
                                 c->stream));
     }
+    if (trace) t_upd += ms_since(tu);
   }
+  if (trace)
+    std::fprintf(stderr, "mixed solve: FP64 residuals %.2f ms, batched CG %.2f ms, updates %.2f ms, total %.2f ms\n",
+                 t_res, t_bcg, t_upd, ms_since(t0));
   for (int l = 0; l < n; ++l) {
     if (std::getenv("ND_TRACE"))
       std::fprintf(stderr, "mixed solve: shift %d sigma %.3e sloppy resid %.3e outer %d final %.3e\n", l, sigma[l],

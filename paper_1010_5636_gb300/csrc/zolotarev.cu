@@ -13,7 +13,12 @@
 // Jacobi functions by the arithmetic-geometric mean (Abramowitz & Stegun 16.4), started from
 // the complementary parameter eps itself so that kappa' close to 1 loses no digits; long
 // double throughout.
+#include <algorithm>
 #include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "../../include/nd.h"
@@ -61,8 +66,50 @@ ld rhat(ld t, const std::vector<ld>& c, int n) {
 
 }  // namespace
 
+namespace {
+// Tables already computed in this process, keyed by (n, eps bits): the extended-precision
+// computation is slow on hosts whose long double is emulated in software, and D_N asks for the
+// same table on every application.
+struct ZoloEntry {
+  std::vector<double> sigma, b;
+  double delta;
+};
+std::mutex g_zmutex;
+std::map<std::pair<int, uint64_t>, ZoloEntry> g_zcache;
+}  // namespace
+
+static nd_status zolotarev_compute(int n, double eps, double* sigma, double* b, double* delta);
+
 extern "C" nd_status nd_zolotarev(int n, double eps, double* sigma, double* b, double* delta) {
   if (n < 1 || n > 64 || !(eps > 0.0 && eps < 1.0) || !sigma || !b) return ND_ERR_INVALID_ARG;
+  uint64_t bits;
+  std::memcpy(&bits, &eps, sizeof(bits));
+  const auto key = std::make_pair(n, bits);
+  {
+    std::lock_guard<std::mutex> lock(g_zmutex);
+    auto it = g_zcache.find(key);
+    if (it != g_zcache.end()) {
+      std::copy(it->second.sigma.begin(), it->second.sigma.end(), sigma);
+      std::copy(it->second.b.begin(), it->second.b.end(), b);
+      if (delta) *delta = it->second.delta;
+      return ND_OK;
+    }
+  }
+  double d = 0.0;
+  const nd_status st = zolotarev_compute(n, eps, sigma, b, &d);
+  if (st != ND_OK) return st;
+  if (delta) *delta = d;
+  std::lock_guard<std::mutex> lock(g_zmutex);
+  ZoloEntry e;
+  e.sigma.assign(sigma, sigma + n);
+  e.b.assign(b, b + n);
+  e.delta = d;
+  if (g_zcache.size() > 256) g_zcache.clear();
+  g_zcache[key] = e;
+  return ND_OK;
+}
+
+static nd_status zolotarev_compute(int n, double eps, double* sigma, double* b, double* delta) {
   const ld e = (ld)eps;
   const ld m = 1.0L - e;
   const ld Kp = ellip_k(e);
