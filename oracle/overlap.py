@@ -14,10 +14,12 @@ Test infrastructure only.
   Hermitian; ``two_sided=False`` gives the paper's literal left-only form.
   ||Q||^2 is passed in as lam_max (an upper estimate of lambda_max(Q^2)); eps is the lower
   end of the approximation interval of X^2.
+  ``sign_apply_poly`` is the same deflated operator with the paper's own minmax polynomial
+  X P_n(X^2) evaluated by the Clenshaw recurrence (oracle/chebyshev.py) in place of R.
 """
 import numpy as np
 
-from . import mscg, wilson, zolotarev
+from . import chebyshev, mscg, wilson, zolotarev
 
 _zcache = {}
 
@@ -61,10 +63,45 @@ def sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u=None, nu=None, two_
     return z, info
 
 
+_ccache = {}
+
+
+def cheb(degree, eps):
+    key = (int(degree), float(eps))
+    if key not in _ccache:
+        _ccache[key] = chebyshev.minmax(int(degree), float(eps))
+    return _ccache[key]
+
+
+def sign_apply_poly(U, dims, m, eta, lam_max, eps, degree, u=None, nu=None, two_sided=True, antiperiodic_t=False):
+    """sign(Q) eta ~ P_+ - P_- + (1 - P) X P_n(X^2) (1 - P) eta (two-sided) with the minmax
+    polynomial of the given degree on [eps, 1]; ``two_sided=False`` drops the right projector."""
+    Q = lambda v: wilson.apply_Q(U, np.ascontiguousarray(v), dims, m, antiperiodic_t)
+    coef = cheb(degree, eps)
+    l = 0 if nu is None else len(nu)
+    if l:
+        c = np.array([np.vdot(u[k], eta) for k in range(l)])
+        eta_perp = eta - np.einsum("k,k...->...", c, u)
+    else:
+        c = np.zeros(0, dtype=np.complex128)
+        eta_perp = eta
+    src = eta_perp if (two_sided or not l) else eta
+    y = chebyshev.poly_apply(lambda v: Q(Q(v)) / lam_max, coef["c"], eps, src)
+    z = Q(y) / np.sqrt(lam_max)
+    if l:
+        cz = np.array([np.vdot(u[k], z) for k in range(l)])
+        z = z - np.einsum("k,k...->...", cz, u) + np.einsum("k,k...->...", np.sign(nu) * c, u)
+    return z, {"delta": coef["delta"], "degree": int(degree)}
+
+
 def dn_apply(U, dims, m, s, eta, lam_max, eps, npoles, tol, u=None, nu=None, m_q=0.0, two_sided=True,
-             antiperiodic_t=False):
-    """D_N^m eta = (1 - abar m_q/2) (1 + s) (eta + gamma5 sign(Q) eta) + m_q eta."""
-    sg, info = sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u, nu, two_sided, antiperiodic_t)
+             antiperiodic_t=False, degree=None):
+    """D_N^m eta = (1 - abar m_q/2) (1 + s) (eta + gamma5 sign(Q) eta) + m_q eta.  With ``degree``
+    given, sign(Q) uses the minmax polynomial of that degree instead of the Zolotarev function."""
+    if degree is None:
+        sg, info = sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u, nu, two_sided, antiperiodic_t)
+    else:
+        sg, info = sign_apply_poly(U, dims, m, eta, lam_max, eps, degree, u, nu, two_sided, antiperiodic_t)
     abar = 1.0 / (1.0 + s)
     dn = (eta + gamma5(sg)) / abar
     return (1.0 - abar * m_q / 2.0) * dn + m_q * eta, info
