@@ -15,8 +15,9 @@ Readings (the paper is silent on them):
     sqrt(y_i) P(y_i) + (-1)^i E = 1 on the current reference y_0 < ... < y_{n+1}, then moves the
     reference to the extrema of h between the zeros of h.
 
-Pinned in tests/test_oracle_chebyshev.py: n = 0 closed form, brute-force minimisation at n = 1,
-the alternation property, the uniform bound against dense sign(Q) = V sgn(Lambda) V^dagger, and
+Pinned in tests/test_oracle_chebyshev.py: n = 0 closed form, a linear-programming solution of the
+discretised minimax problem at small n, convexity (no perturbation improves), the alternation
+property, the uniform bound against dense sign(Q) = V sgn(Lambda) V^dagger, and
 the Clenshaw recurrence against numpy's Chebyshev series evaluation on the eigenvalues.
 """
 import numpy as np
@@ -69,15 +70,26 @@ def _extremum(c, eps, lo, hi, samples=48):
 
 
 def minmax(n, eps, rtol=1e-9, atol=2e-14, maxiter=200):
-    """Minmax coefficients of degree n on [eps, 1]: returns dict(c=array[n+1], delta, ref, iters).
-    Stops when the extrema of |h| agree to rtol relative or atol absolute (h itself is only
-    known to a few 1e-15 in FP64, which bounds the levelling of small delta)."""
+    """Minmax coefficients of degree n on [eps, 1]: returns dict(c=array[n+1], delta, ref, iters,
+    resolved).  Stops when the extrema of |h| agree to rtol relative or atol absolute (h itself is
+    only known to a few 1e-15 in FP64, which bounds the levelling of small delta).  When delta is
+    at that rounding level the alternation cannot be resolved: resolved = False and delta is the
+    largest |h| on a fine grid (an upper estimate, not the minmax value)."""
     if n < 0 or not (0.0 < eps < 1.0):
         raise ValueError("need n >= 0 and 0 < eps < 1")
     # start from the Chebyshev extrema of degree n + 1 mapped onto [eps, 1]
     yref = 0.5 * (1.0 + eps) - 0.5 * (1.0 - eps) * np.cos(np.pi * np.arange(n + 2) / (n + 1))
     for it in range(1, maxiter + 1):
         c, E = _solve_reference(yref, n, eps)
+        hr = h_eval(c, yref, eps)
+        if np.any(hr[1:] * hr[:-1] >= 0):
+            # the levelled error is at the rounding level of h: the alternation can no longer be
+            # resolved in FP64; report the largest |h| on a fine grid as delta
+            if abs(E) > 1e-12:
+                raise RuntimeError("Remez exchange lost the alternation")
+            grid = 0.5 * (1 + eps) - 0.5 * (1 - eps) * np.cos(np.linspace(0, np.pi, 20 * (n + 2)))
+            return {"c": c, "delta": float(np.max(np.abs(h_eval(c, grid, eps)))), "ref": yref, "iters": it,
+                    "resolved": False}
         # zeros of h between consecutive reference points (h alternates there by construction)
         roots = [brentq(lambda t: float(h_eval(c, t, eps)), yref[i], yref[i + 1], xtol=1e-16, rtol=1e-15)
                  for i in range(n + 1)]
@@ -87,7 +99,8 @@ def minmax(n, eps, rtol=1e-9, atol=2e-14, maxiter=200):
         yref = ynew
         if hv.max() - hv.min() <= max(rtol * hv.max(), atol):
             c, E = _solve_reference(yref, n, eps)
-            return {"c": c, "delta": float(np.abs(h_eval(c, yref, eps)).max()), "ref": yref, "iters": it}
+            return {"c": c, "delta": float(np.abs(h_eval(c, yref, eps)).max()), "ref": yref, "iters": it,
+                    "resolved": True}
     raise RuntimeError("Remez exchange did not converge")
 
 

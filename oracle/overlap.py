@@ -105,3 +105,34 @@ def dn_apply(U, dims, m, s, eta, lam_max, eps, npoles, tol, u=None, nu=None, m_q
     abar = 1.0 / (1.0 + s)
     dn = (eta + gamma5(sg)) / abar
     return (1.0 - abar * m_q / 2.0) * dn + m_q * eta, info
+
+
+def propagator(U, dims, m, s, b, lam_max, eps, npoles, tol_inner, u=None, nu=None, m_q=0.1, tol=1e-10,
+               maxit=10000, degree=None):
+    """x = (D_N^m)^{-1} b by CG on the normal equations D D^dagger y = b, x = D^dagger y, with
+    D^dagger = gamma5 D gamma5 (exact for the two-sided, hermitian approximation of sign(Q)).
+    Stops at ||b - D D^dagger y|| <= tol ||b||.  Returns x and dict(iters, resid) with resid the
+    true relative residual ||b - D x|| / ||b||."""
+    D = lambda v: dn_apply(U, dims, m, s, v, lam_max, eps, npoles, tol_inner, u, nu, m_q, degree=degree)[0]
+    Dd = lambda v: gamma5(D(gamma5(v)))
+    DDd = lambda v: D(Dd(v))
+    y = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    bn = np.sqrt(np.vdot(b, b).real)
+    it = 0
+    while np.sqrt(rr) > tol * bn:
+        if it >= maxit:
+            raise RuntimeError("propagator CG did not converge")
+        w = DDd(p)
+        alpha = rr / np.vdot(p, w).real
+        y = y + alpha * p
+        r = r - alpha * w
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        it += 1
+    x = Dd(y)
+    res = np.linalg.norm(b - D(x)) / bn
+    return x, {"iters": it, "resid": float(res)}

@@ -147,3 +147,11 @@ def test_poly_sign_deflated_and_dn(lat2):
     dz, iz = overlap.dn_apply(U, dims, M, 0.4, eta, lam_max, eps, 16, 1e-12, lm["u"], lm["nu"])
     dp, ip = overlap.dn_apply(U, dims, M, 0.4, eta, lam_max, eps, 16, 1e-12, lm["u"], lm["nu"], degree=40)
     assert np.linalg.norm(dz - dp) <= 1.4 * (iz["delta"] + ip["delta"] + 1e-10) * np.linalg.norm(eta)
+
+
+def test_rounding_level_delta_is_flagged():
+    # at this degree the minmax error (~1e-16) is below what FP64 resolves: flagged, bounded
+    r = chebyshev.minmax(256, 5.34e-3)
+    assert r["resolved"] is False
+    assert r["delta"] <= 1e-13
+    assert chebyshev.minmax(40, 1e-2)["resolved"] is True

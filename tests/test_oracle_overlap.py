@@ -154,3 +154,25 @@ def test_dn_error_bound(lat2, noise):
         worst = max(worst, err)
     extra = (1 + S) * (1 - abar * mq / 2) * (info["delta"] + 1e-9)
     assert worst <= bound + extra
+
+
+@pytest.mark.parametrize("m_q", [0.2, 0.05])
+def test_propagator_vs_dense(lat2, m_q):
+    """(D_N^m)^{-1} b by the oracle's CG against LAPACK solve of the dense D_N^m built from the
+    exact sign(Q); the difference is bounded by the approximation error of sign(Q) (delta), the
+    CG tolerance and ||(D_N^m)^{-1}|| <= 1/m_q (the massive overlap spectrum lies on a circle
+    shifted away from 0 by m_q)."""
+    dims, U, lm, S_ex, lam_max, eps = lat2
+    b = synth.spinor(dims, seed=9)
+    x, info = overlap.propagator(U, dims, M, S, b, lam_max, eps, 16, 1e-13, lm["u"], lm["nu"], m_q=m_q, tol=1e-11)
+    assert b.dtype == np.complex128
+    n = b.size
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), n // 12)
+    abar = 1.0 / (1.0 + S)
+    D_ex = (1.0 - abar * m_q / 2.0) * (1.0 + S) * (np.eye(n) + g5[:, None] * S_ex) + m_q * np.eye(n)
+    x_ex = np.linalg.solve(D_ex, b.reshape(-1))
+    assert info["resid"] <= 2e-11
+    # ||x - x_ex|| <= ||D_ex^{-1}|| (||b - D x|| + ||(D - D_ex) x||), ||D - D_ex|| <= (1 + s)(delta + CG error)
+    delta = overlap.zolo(16, eps)["delta"]
+    bound = (info["resid"] * np.linalg.norm(b) + (1 + S) * (delta + 1e-12) * np.linalg.norm(x)) / m_q
+    assert np.linalg.norm(x.reshape(-1) - x_ex) <= bound
