@@ -383,11 +383,60 @@ def dn_phase(nd, torch, reps):
         res[name] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "krylov_iters": info.iters,
                      "sloppy_iters": info.sloppy_iters, "refinement_sweeps": info.outer,
                      "max_shift_resid": info.max_resid, "delta_zolotarev": info.delta, "eps": info.eps}
+    # the paper's own approximation: minmax polynomial of the smallest degree with delta <= 1e-10,
+    # Clenshaw recurrence in FP64 or FP32 (no refinement)
+    for name, inner in (("poly_fp64", 0), ("poly_fp32", 1)):
+        p = nd.dn_params(0, 0.0, 0.0, 1e-10, 1, inner, 0.0, False, approx=nd.ND_SIGN_CHEBYSHEV)
+        o = torch.empty_like(eta)
+        info = nd.nd_apply_DN(ctx, o, eta, p)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = nd.nd_apply_DN(ctx, o, eta, p)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        outs[name] = o.clone()
+        res[name] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "degree": info.degree,
+                     "delta_poly": info.delta, "eps": info.eps}
     base = outs["fp64"]
-    for name in ("mixed_fp32", "mixed_fp16"):
+    for name in ("mixed_fp32", "mixed_fp16", "poly_fp64", "poly_fp32"):
         res[name]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs[name] - base) /
                                               torch.linalg.vector_norm(base))
         res[name]["speedup_vs_fp64"] = round(res["fp64"]["s_per_apply"] / res[name]["s_per_apply"], 3)
+    nd.nd_destroy(ctx)
+    return res
+
+
+def clenshaw_phase(nd, torch, degree=200, reps=3):
+    """The paper's D_N timing unit: time per Clenshaw iteration per lattice site, 24^3x48
+    near-identity links (eps 0.3, seed 0), undeflated sign(Q) with the minmax polynomial of the
+    given degree on [0.01, 1], FP32 and FP64 recurrences (whole D_N apply / (degree * V))."""
+    import numpy as np
+
+    import synth
+    dims = (48, 24, 24, 24)
+    V = int(np.prod(dims))
+    U = torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda()
+    eta = torch.from_numpy(synth.spinor(dims, seed=1)).cuda()
+    ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, U, (18, 12, 12))
+    res = {"workload": f"D_N by Clenshaw, 24^3x48 near-identity links, degree {degree}, eps 0.01, no deflation"}
+    for name, inner in (("fp32", 1), ("fp64", 0)):
+        p = nd.dn_params(0, 0.01, 0.0, 1e-10, 1, inner, 0.0, False, approx=nd.ND_SIGN_CHEBYSHEV, degree=degree)
+        o = torch.empty_like(eta)
+        nd.nd_apply_DN(ctx, o, eta, p)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = nd.nd_apply_DN(ctx, o, eta, p)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        res[name] = {"s_per_apply": round(t, 5), "us_per_iteration_per_site": t / (degree * V) * 1e6,
+                     "delta_poly": info.delta}
     nd.nd_destroy(ctx)
     return res
 
@@ -577,6 +626,7 @@ def main():
         line["sweep"] = sweep_phase(nd, torch)
     if not args.no_dn:
         line["dn"] = dn_phase(nd, torch, args.dn_reps)
+        line["clenshaw"] = clenshaw_phase(nd, torch)
     if not args.no_extra:
         line["multi_rhs"] = mrhs_phase(nd, torch)
         line["force"] = force_phase(nd, torch)

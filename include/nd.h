@@ -194,6 +194,19 @@ nd_status nd_lambda_max(nd_ctx* ctx, int iters, double* lambda_max);
  * (host computation; n poles).  Returns the uniform error delta.  Host arrays sigma[n], b[n]. */
 nd_status nd_zolotarev(int n, double eps, double* sigma, double* b, double* delta);
 
+/* Minmax polynomial of Sec. 2.2: P_n(y) = sum_{k=0}^{n} c_k T_k(z), z = (2y - 1 - eps)/(1 - eps),
+ * minimising delta = max_{eps <= y <= 1} |1 - sqrt(y) P_n(y)|, so that x P_n(x^2) ~ sign(x) on
+ * sqrt(eps) <= |x| <= 1 with uniform error delta (host computation, Remez exchange; tables
+ * are cached per (degree, eps)).  c: host array [degree + 1]; 0 <= degree <= 2048.
+ * ND_ERR_NOT_CONVERGED if the exchange does not level the error. */
+nd_status nd_chebyshev(int degree, double eps, double* c, double* delta);
+
+/* Smallest degree n with delta(n) <= delta_target on [eps, 1] (ND_ERR_INVALID_ARG if above 2048). */
+nd_status nd_chebyshev_degree(double eps, double delta_target, int* degree);
+
+/* Approximation of sign(Q) used by nd_apply_sign / nd_apply_DN. */
+enum { ND_SIGN_ZOLOTAREV = 0, ND_SIGN_CHEBYSHEV = 1 };
+
 typedef struct {
   int n_poles;         /* Zolotarev poles (shifted systems) */
   double eps;          /* lower end of the X^2 interval; 0 = 0.99 * lambda_next / lambda_max */
@@ -203,6 +216,11 @@ typedef struct {
   nd_prec inner_prec;  /* ND_FP64: pure FP64; ND_FP32/ND_FP16: sloppy Krylov + FP64 refinement */
   double m_q;          /* quark mass of D_N^m = (1 - abar m_q / 2) D_N + m_q (0 = massless) */
   int left_only;       /* 1: the paper's literal (1 - P) X R(X^2) eta; 0: (1 - P) X R(X^2) (1 - P) eta */
+  int approx;          /* ND_SIGN_ZOLOTAREV (rational, multi-shift CG) or ND_SIGN_CHEBYSHEV (the
+                          paper's minmax polynomial X P_n(X^2) by the Clenshaw recurrence) */
+  int degree;          /* ND_SIGN_CHEBYSHEV: degree n of P_n; 0 = smallest n with delta <= tol.
+                          n_poles and maxit are not used; inner_prec is the precision of the whole
+                          recurrence (no refinement: FP32 gives ~1e-6, FP16 ~1e-3 relative) */
 } nd_dn_params;
 
 typedef struct {
@@ -210,21 +228,42 @@ typedef struct {
   int sloppy_iters;    /* total sloppy iterations including refinement */
   int outer;           /* FP64 refinement sweeps */
   int n_low;           /* deflated modes used */
-  double delta;        /* Zolotarev uniform error on [sqrt(eps), 1] */
+  double delta;        /* uniform error of the approximation on [sqrt(eps), 1] */
   double eps;          /* eps used */
   double lambda_max;   /* lambda_max used */
   double max_resid;    /* max over shifts of the FP64 relative residual of the shifted solves */
   double time_ms;
+  int degree;          /* ND_SIGN_CHEBYSHEV: degree of P_n used (Clenshaw iterations); else 0 */
 } nd_dn_info;
 
-/* out = sign(Q) in with the deflated Zolotarev approximation
+/* out = sign(Q) in with the deflated approximation
  *   sign(Q) ~ P_+ - P_- + (1 - P) X R(X^2) (1 - P),  X = Q / sqrt(lambda_max)   (Sec. 2.3),
+ * R the Zolotarev function or the minmax polynomial P_n (p->approx),
  * using the context's low modes (none if nd_lowmodes/nd_set_lowmodes was not called).
  * in_dev/out_dev: canonical FP64 device spinors (may not overlap). */
 nd_status nd_apply_sign(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p, nd_dn_info* info);
 
 /* out = D_N^m in, D_N = (1 + gamma5 sign(Q)) / abar, abar = 1/(1 + s)  (Sec. 2.2, 2.3). */
 nd_status nd_apply_DN(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p, nd_dn_info* info);
+
+/* ---------------------------------------------------------------- propagators */
+
+typedef struct {
+  int iters;           /* outer CG iterations (one sign(Q) application each), both chiralities */
+  int sign_iters;      /* Krylov iterations (Zolotarev) or Clenshaw iterations (Chebyshev) of all sign(Q) applications */
+  double resid;        /* true relative residual ||b - D_N^m x|| / ||b|| (with the same approximate sign(Q)) */
+  double time_ms;
+} nd_prop_info;
+
+/* x = (D_N^m)^{-1} b for the massive overlap operator D_N^m = (1 - abar m_q/2) D_N + m_q (Sec. 2.2).
+ * D_N^m is normal for a hermitian sign(Q), and H = D_N^m D_N^m^dagger commutes with gamma5; each
+ * chirality of b is solved by CG on H (one sign(Q) application per iteration, approximation,
+ * deflation and inner precision as in p) to ||P_c b - H y_c|| <= tol ||P_c b||, and
+ * x = gamma5 D_N^m gamma5 y.  p->left_only must be 0 (the left-only form is not hermitian).
+ * b_dev, x_dev: canonical FP64 device spinors (may not overlap).  ND_ERR_NOT_CONVERGED after
+ * maxit iterations of either chirality (x holds the last iterate); m_q > 0 keeps H >= m_q^2. */
+nd_status nd_propagator(nd_ctx* ctx, double* x_dev, const double* b_dev, const nd_dn_params* p, double tol,
+                        int maxit, nd_prop_info* info);
 
 /* ---------------------------------------------------------------- differentiation */
 

@@ -41,13 +41,20 @@ class nd_lowmode_info(ctypes.Structure):
 class nd_dn_params(ctypes.Structure):
     _fields_ = [("n_poles", ctypes.c_int), ("eps", ctypes.c_double), ("lambda_max", ctypes.c_double),
                 ("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_prec", ctypes.c_int),
-                ("m_q", ctypes.c_double), ("left_only", ctypes.c_int)]
+                ("m_q", ctypes.c_double), ("left_only", ctypes.c_int), ("approx", ctypes.c_int),
+                ("degree", ctypes.c_int)]
 
 
 class nd_dn_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("sloppy_iters", ctypes.c_int), ("outer", ctypes.c_int),
                 ("n_low", ctypes.c_int), ("delta", ctypes.c_double), ("eps", ctypes.c_double),
-                ("lambda_max", ctypes.c_double), ("max_resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("lambda_max", ctypes.c_double), ("max_resid", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("degree", ctypes.c_int)]
+
+
+class nd_prop_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("sign_iters", ctypes.c_int), ("resid", ctypes.c_double),
+                ("time_ms", ctypes.c_double)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64
@@ -74,6 +81,9 @@ _SIGS = {
     "nd_get_lowmodes": ([_P, _P, _P], _I),
     "nd_lambda_max": ([_P, _I, ctypes.POINTER(_D)], _I),
     "nd_zolotarev": ([_I, _D, _P, _P, ctypes.POINTER(_D)], _I),
+    "nd_chebyshev": ([_I, _D, _P, ctypes.POINTER(_D)], _I),
+    "nd_propagator": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), _D, _I, ctypes.POINTER(nd_prop_info)], _I),
+    "nd_chebyshev_degree": ([_D, _D, ctypes.POINTER(_I)], _I),
     "nd_apply_sign": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_apply_DN": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_force": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
@@ -261,10 +271,27 @@ def nd_zolotarev(n, eps):
     return list(sig), list(b), d.value
 
 
+def nd_chebyshev(degree, eps):
+    """Minmax coefficients c[0..degree] of P_n on [eps, 1] and the uniform error delta."""
+    c = (ctypes.c_double * (int(degree) + 1))()
+    d = ctypes.c_double()
+    _check(None, lib().nd_chebyshev(int(degree), float(eps), ctypes.cast(c, _P), ctypes.byref(d)), "nd_chebyshev")
+    return list(c), d.value
+
+
+def nd_chebyshev_degree(eps, delta_target):
+    n = ctypes.c_int()
+    _check(None, lib().nd_chebyshev_degree(float(eps), float(delta_target), ctypes.byref(n)), "nd_chebyshev_degree")
+    return n.value
+
+
+ND_SIGN_ZOLOTAREV, ND_SIGN_CHEBYSHEV = 0, 1
+
+
 def dn_params(n_poles=16, eps=0.0, lambda_max=0.0, tol=1e-12, maxit=100000, inner_prec=ND_FP64, m_q=0.0,
-              left_only=False):
+              left_only=False, approx=ND_SIGN_ZOLOTAREV, degree=0):
     return nd_dn_params(int(n_poles), float(eps), float(lambda_max), float(tol), int(maxit), int(inner_prec),
-                        float(m_q), int(left_only))
+                        float(m_q), int(left_only), int(approx), int(degree))
 
 
 def nd_apply_sign(ctx, out, inp, params):
@@ -278,6 +305,14 @@ def nd_apply_DN(ctx, out, inp, params):
     info = nd_dn_info()
     _check(ctx, lib().nd_apply_DN(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params), ctypes.byref(info)),
            "nd_apply_DN")
+    return info
+
+
+def nd_propagator(ctx, x, b, params, tol=1e-10, maxit=10000):
+    """x = (D_N^m)^{-1} b (canonical FP64 device tensors); returns nd_prop_info."""
+    info = nd_prop_info()
+    _check(ctx, lib().nd_propagator(ctx, _ptr(_f64(x)), _ptr(_f64(b)), ctypes.byref(params), float(tol), int(maxit),
+                                    ctypes.byref(info)), "nd_propagator")
     return info
 
 

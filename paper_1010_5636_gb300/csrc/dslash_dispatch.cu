@@ -43,7 +43,7 @@ cudaError_t launch_q(const Geom& g, const QLaunch& L0, cudaStream_t st) {
   if (L.mode == Q_MRHS && (L.nrhs < 1 || L.reduce)) return cudaErrorInvalidValue;
   if ((L.mode == Q_BPLAIN || L.mode == Q_BCG) && (L.nrhs < 1 || !L.reduce)) return cudaErrorInvalidValue;
   if (L.split == 0) L.split = default_split(L.prec, L.recon, L.nsites != 2 * g.Vh);
-  if (L.mode == Q_MRHS || L.mode == Q_BPLAIN || L.mode == Q_BCG) L.split = 1;
+  if (L.mode == Q_MRHS || L.mode == Q_BPLAIN || L.mode == Q_BCG || L.mode == Q_XPAY3) L.split = 1;
   if (L.split != 1 && L.split != 2 && L.split != 4) return cudaErrorInvalidValue;
   switch (L.prec) {
     case 0: return launch_q_fp64(g, L, st);

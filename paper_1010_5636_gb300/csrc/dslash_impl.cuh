@@ -122,13 +122,14 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
   const double b_d = BASE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
   const T diag = (T)A.diag, ca = (T)a_d, cb = (T)b_d;
   const bool read_diag = REDUCE || A.diag != 0.0;
-  constexpr bool IN_PLACE = BASE == Q_CGUPDATE || BASE == Q_XPAY2;
-  Spinor<T> d, y, z;
+  constexpr bool IN_PLACE = BASE == Q_CGUPDATE || BASE == Q_XPAY2 || BASE == Q_XPAY3;
+  Spinor<T> d, y, z, w;
   if (act) {
     if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
     if (BASE != Q_PLAIN || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
     if (BASE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
-    if (BASE == Q_XPAY2) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
+    if (BASE == Q_XPAY2 || BASE == Q_XPAY3) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
+    if (BASE == Q_XPAY3) SpinorIO<P>::load(w, A.w, g.Vh, p, h);
   }
   // in the in-place modes every part must have read its copy of z before any part of the
   // block stores (each site's chunks are written by different warps)
@@ -157,6 +158,13 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
       for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) res.s[a][c] = res.s[a][c] + cb * y.s[a][c] + cc * z.s[a][c];
+    } else if (BASE == Q_XPAY3) {
+      const T cc = (T)A.c, cd = (T)A.d;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          res.s[a][c] = res.s[a][c] + cb * y.s[a][c] + cc * z.s[a][c] + cd * w.s[a][c];
     } else {
       const double alpha = A.cgs[CG_RR] / (a_d * A.cgs[CG_TT] + b_d * A.cgs[CG_PP]);
       const T al = (T)alpha;
@@ -223,6 +231,10 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
       return L.reduce ? launch_q4<P, R, Q_XPAY2, true>(g, L, st) : launch_q4<P, R, Q_XPAY2, false>(g, L, st);
     case Q_CGUPDATE:
       return L.reduce ? launch_q4<P, R, Q_CGUPDATE, true>(g, L, st) : launch_q4<P, R, Q_CGUPDATE, false>(g, L, st);
+    case Q_XPAY3:
+      if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
+      if (P == P64 || L.threads == 256) return launch_q5<P, R, Q_XPAY3, false, 1, 256, 1>(g, L, st);
+      return launch_q5<P, R, Q_XPAY3, false, 1, 64, 8>(g, L, st);
     case Q_MRHS:
       if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64 || L.threads == 256) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);

@@ -39,10 +39,12 @@ __host__ __device__ inline int sh(int array, int l) { return CG_NSCALAR + array 
 // Q_MRHS: Q_PLAIN over nrhs fields.  Q_BPLAIN / Q_BCG: Q_PLAIN / Q_CGUPDATE with a reduction,
 // over nrhs independent systems (the batched CG): field r at + r * rhs_stride, its scalar block
 // at cgs + r * cgs_stride, its reduction partials / counter / result offset likewise.
-enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2, Q_MRHS = 3, Q_BPLAIN = 4, Q_BCG = 5 };
+enum QMode { Q_PLAIN = 0, Q_CGUPDATE = 1, Q_XPAY2 = 2, Q_MRHS = 3, Q_BPLAIN = 4, Q_BCG = 5, Q_XPAY3 = 6 };
 
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y      (Q_PLAIN; y may be null)
 // out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y + c * z   (Q_XPAY2; z may alias out)
+// out = a * gamma5 (diag * in - 1/2 hop(in)) + b * y + c * z + d * w
+//                                             (Q_XPAY3, one Clenshaw step; z may alias out)
 // out = out - alpha * (a * gamma5(diag * in - 1/2 hop(in)) + b * y),
 //       alpha = cgs[CG_RR] / (a * cgs[CG_TT] + b * cgs[CG_PP]),
 //       a = cgs[CG_ASCALE], b = cgs[CG_SIGMA0]                       (Q_CGUPDATE)
@@ -57,8 +59,9 @@ struct QLaunch {
   const void* in;
   void* out;
   const void* y;
-  const void* z;  // Q_XPAY2 only
-  double diag, a, b, c;
+  const void* z;  // Q_XPAY2 and Q_XPAY3
+  const void* w;  // Q_XPAY3 only
+  double diag, a, b, c, d;
   int parity0, nsites;
   ReduceSlot slot;
   const double* cgs;  // multi-shift CG scalars, or null; kernels skip when cgs[CG_DONE] or cgs[CG_PENDING] != 0

@@ -14,12 +14,15 @@
 namespace nd {
 
 nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a, double b, const void* y, double* result,
-                  const double* cgs, const void* z, double cz) {
+                  const double* cgs, const void* z, double cz, const void* w, double cw) {
   if (!c->links[prec]) return fail(c, ND_ERR_STATE, "links are not set in the precision this call needs");
+  if (w && (!z || result)) return fail(c, ND_ERR_INVALID_ARG, "q_apply: w needs z and no reduction");
   QLaunch L{};
   L.prec = prec;
   L.recon = c->recon[prec];
-  L.mode = z ? Q_XPAY2 : Q_PLAIN;
+  L.mode = w ? Q_XPAY3 : (z ? Q_XPAY2 : Q_PLAIN);
+  L.w = w;
+  L.d = cw;
   L.reduce = result != nullptr;
   L.links = c->links[prec];
   L.in = in;

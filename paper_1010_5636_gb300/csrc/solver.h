@@ -6,11 +6,11 @@
 
 namespace nd {
 
-// out = a * Q in + b * y + cz * z (internal fields of precision prec; z may alias out).  With result != null the launch
-// also reduces ||out||^2 and ||in||^2 into result[0..1].
+// out = a * Q in + b * y + cz * z + cw * w (internal fields of precision prec; z may alias out).  With result != null
+// the launch also reduces ||out||^2 and ||in||^2 into result[0..1] (not with w).
 nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a = 1.0, double b = 0.0,
                   const void* y = nullptr, double* result = nullptr, const double* cgs = nullptr,
-                  const void* z = nullptr, double cz = 0.0);
+                  const void* z = nullptr, double cz = 0.0, const void* w = nullptr, double cw = 0.0);
 
 // Device buffer for one internal field of `prec`, cached under `name`.
 void* field(nd_ctx* c, const char* name, int prec, int count = 1);
@@ -57,6 +57,10 @@ nd_status mixed_solve(nd_ctx* c, int ps, const void* b64, double bnorm2, const s
       c, ps, b64, bnorm2, sigma, tol, ascale, maxit, st,
       [](void* ctx, int l, void* x) -> nd_status { return (*static_cast<Sink*>(ctx))(l, x); }, &sink);
 }
+
+// sign(Q) in64 (internal FP64 layout) with the deflated approximation of p; *sign64 points to a
+// context workspace holding the result (internal FP64) until the next sign application.
+nd_status sign_internal(nd_ctx* c, const void* in64, const nd_dn_params* p, nd_dn_info* info, void** sign64);
 
 // Hermitian eigenproblem (cyclic Jacobi): A (n x n, row-major complex as re/im pairs) is
 // overwritten; evals ascending, evecs column k = eigenvector k (row-major, re/im pairs).
