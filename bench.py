@@ -400,6 +400,17 @@ def dn_phase(nd, torch, reps):
         outs[name] = o.clone()
         res[name] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "degree": info.degree,
                      "delta_poly": info.delta, "eps": info.eps}
+    # massive overlap propagator of one point source (origin, spin 0, colour 0), m_q = 0.1,
+    # mixed FP32 sign(Q) to 1e-12, outer CG to 1e-10
+    b = torch.zeros_like(eta)
+    b.view(-1, 4, 3)[0, 0, 0] = 1.0
+    x = torch.empty_like(eta)
+    p = nd.dn_params(20, 0.0, 0.0, 1e-12, 200000, 1, 0.1, False)
+    t0 = time.perf_counter()
+    pinf = nd.nd_propagator(ctx, x, b, p, tol=1e-10, maxit=1000)
+    t = time.perf_counter() - t0
+    res["propagator"] = {"s": round(t, 3), "outer_iters": pinf.iters, "sign_krylov_iters": pinf.sign_iters,
+                         "resid": pinf.resid, "m_q": 0.1, "inner": "mixed_fp32, sign to 1e-12"}
     base = outs["fp64"]
     for name in ("mixed_fp32", "mixed_fp16", "poly_fp64", "poly_fp32"):
         res[name]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs[name] - base) /
@@ -454,6 +465,18 @@ def profile_case(nd, torch, case):
         nd.nd_pack_spinor(ctx, a, torch.from_numpy(synth.spinor(dims, seed=1)).cuda(), 1)
         for _ in range(3):
             nd.nd_apply_Q_parity(ctx, b, a, 1, 0, 0.0)
+        torch.cuda.synchronize()
+        nd.nd_destroy(ctx)
+    elif case == "clen24":
+        # sign(Q) by a degree-4 Clenshaw recurrence in FP32 on 24^3x48 (no deflation): 4 plain Q
+        # launches and 3 fused Clenshaw-step launches (Q_XPAY3), about 1 GB on the device
+        dims = (48, 24, 24, 24)
+        U = torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda()
+        eta = torch.from_numpy(synth.spinor(dims, seed=1)).cuda()
+        ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+        nd.nd_set_links(ctx, U, (18, RECON, 0))
+        o = torch.empty_like(eta)
+        nd.nd_apply_sign(ctx, o, eta, nd.dn_params(0, 0.01, 30.0, 1e-10, 1, 1, approx=nd.ND_SIGN_CHEBYSHEV, degree=4))
         torch.cuda.synchronize()
         nd.nd_destroy(ctx)
     else:
@@ -559,6 +582,24 @@ def force_phase(nd, torch, reps=2):
     res["mixed_fp32"]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs["mixed_fp32"] - outs["fp64"]) /
                                                   torch.linalg.vector_norm(outs["fp64"]))
     res["mixed_fp32"]["speedup_vs_fp64"] = round(res["fp64"]["s_per_gradient"] / res["mixed_fp32"]["s_per_gradient"], 3)
+    # the solve alone: whole-lattice CG on Q^2 against the even-odd Schur-complement route
+    x = torch.empty_like(phi)
+    solves = {}
+    for name, fn in (("full_fp64", lambda: nd.nd_solve(ctx, [x], phi, [0.0], 1e-10, 100000, 0)),
+                     ("full_mixed_fp32", lambda: nd.nd_solve(ctx, [x], phi, [0.0], 1e-10, 100000, 1)),
+                     ("schur_fp64", lambda: nd.nd_solve_Q2_eo(ctx, x, phi, 1e-10, 100000, 0)),
+                     ("schur_mixed_fp32", lambda: nd.nd_solve_Q2_eo(ctx, x, phi, 1e-10, 100000, 1))):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        solves[name] = {"s": round(float(np.median(ts)), 4), "iters": info.iters, "sweeps": info.outer,
+                        "resid": info.max_resid}
+    res["solve_Q2"] = solves
     nd.nd_destroy(ctx)
     return res
 
@@ -574,7 +615,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS and force measurements")
     ap.add_argument("--dn-reps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--case", default=None, help="run a small profiling case and exit (hop24)")
+    ap.add_argument("--case", default=None, help="run a small profiling case and exit (hop24, clen24)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -155,6 +155,25 @@ typedef struct {
 nd_status nd_solve(nd_ctx* ctx, double* const* x_dev, const double* b_dev, const double* shifts, int n,
                    double tol, int maxit, nd_prec inner, nd_solve_info* info);
 
+/* ---------------------------------------------------------------- even-odd preconditioning */
+
+/* out_e = Qhat in_e with the Schur complement of the even sites (Sec. 2.1 even-odd splitting):
+ *   Qhat = gamma5 [(4 + m) - D_eo D_oe / (4 + m)],  hermitian like Q.
+ * in/out: internal fields of precision prec (nd_spinor_bytes); only their even halves (parity 0,
+ * the first half of the field) are read and written, the odd halves are left as they are.
+ * out and in must differ.  Two one-parity stencil launches. */
+nd_status nd_apply_Qhat(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec);
+
+/* x = (Q^2)^{-1} b through the Schur complement: Q^2 = D_W^dagger D_W, so
+ * (Q^2)^{-1} b = D_W^{-1} gamma5 D_W^{-1} gamma5 b, and each D_W^{-1} is a CG on Qhat^2 over the
+ * even sites plus one launch for the odd sites.  An FP64 defect correction on Q^2 wraps the two
+ * solves, which run in `inner` (FP64, or FP32 / FP16 storage); stops at ||b - Q^2 x|| <= tol ||b||.
+ * b_dev, x_dev: canonical FP64 device spinors (may not overlap).  info->iters counts Qhat^2 CG
+ * iterations, info->outer the defect-correction sweeps, info->max_resid the final FP64 residual.
+ * ND_ERR_NOT_CONVERGED if a CG hits maxit or the correction stagnates (x holds the last iterate). */
+nd_status nd_solve_Q2_eo(nd_ctx* ctx, double* x_dev, const double* b_dev, double tol, int maxit, nd_prec inner,
+                         nd_solve_info* info);
+
 /* ---------------------------------------------------------------- low modes (Sec. 2.3) */
 
 typedef struct {
@@ -175,6 +194,16 @@ typedef struct {
  * Converges each of the l+1 lowest Ritz values of Q^2 to relative residual tol. */
 nd_status nd_lowmodes(nd_ctx* ctx, int l, double tol, int maxit, double* nu, double* rho, double* eval_Q2,
                       nd_lowmode_info* info);
+
+/* Low modes with l chosen dynamically (Sec. 2.3): in [l_min, l_max] the l with the largest relative
+ * gap (sqrt(lambda_{l+1}) - sqrt(lambda_l)) / sqrt(lambda_{l+1}) of the Q^2 Ritz values is taken, so
+ * that the spectral distance of the kept modes from the rest is not accidentally small, and the
+ * iteration stops when kappa_+ and kappa_- (as in nd_lowmodes) are both <= kappa_target.  The
+ * projector deviation of Sec. 2.3 is then <= kappa (1 + 2 kappa) / (1 - 2 kappa (1 + 2 kappa)).
+ * Outputs as nd_lowmodes with l = *l_out modes (host arrays sized for l_max, eval_Q2 for l_max + 1).
+ * ND_ERR_NOT_CONVERGED when maxit Q^2 applications do not reach the target. */
+nd_status nd_lowmodes_dynamic(nd_ctx* ctx, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
+                              double* nu, double* rho, double* eval_Q2, nd_lowmode_info* info);
 
 /* Replace the context's low modes by caller-provided orthonormal vectors (canonical FP64,
  * device, [l][V*12] complex) with their Q eigenvalues nu (host) and an estimate of

@@ -106,3 +106,20 @@ def lowmodes_arpack(U, dims, m, l, antiperiodic_t=False, tol=1e-12):
     basis = vec[:, :l].T.reshape((l,) + shape)
     nu, u, rho = rayleigh_ritz(lambda x: wilson.apply_Q(U, np.ascontiguousarray(x), dims, m, antiperiodic_t), basis)
     return {"nu": nu, "u": u, "rho": rho, "eval_Q2": w, "lam_next": float(w[l]), "lam_max": float(lam_max)}
+
+
+def choose_l(evals_q2, l_min, l_max):
+    """Number of low modes to deflate (Sec. 2.3: chosen dynamically so that the spectral distance
+    to the remaining modes is not accidentally small).  Reading: among l_min <= l <= l_max take the
+    l with the largest relative gap between the last kept and the first remaining mode of Q,
+        g_l = (sqrt(lambda_{l+1}) - sqrt(lambda_l)) / sqrt(lambda_{l+1}),
+    lambda_1 <= lambda_2 <= ... the eigenvalues of Q^2; the smallest such l on ties."""
+    e = np.sqrt(np.asarray(evals_q2, dtype=np.float64))
+    if not (1 <= l_min <= l_max < len(e)):
+        raise ValueError("need 1 <= l_min <= l_max < len(evals)")
+    best, best_g = l_min, -1.0
+    for l in range(l_min, l_max + 1):
+        g = (e[l] - e[l - 1]) / e[l]
+        if g > best_g:
+            best, best_g = l, g
+    return best

@@ -82,6 +82,9 @@ _SIGS = {
     "nd_lambda_max": ([_P, _I, ctypes.POINTER(_D)], _I),
     "nd_zolotarev": ([_I, _D, _P, _P, ctypes.POINTER(_D)], _I),
     "nd_chebyshev": ([_I, _D, _P, ctypes.POINTER(_D)], _I),
+    "nd_apply_Qhat": ([_P, _P, _P, _I], _I),
+    "nd_lowmodes_dynamic": ([_P, _I, _I, _D, _I, ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
+    "nd_solve_Q2_eo": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_propagator": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), _D, _I, ctypes.POINTER(nd_prop_info)], _I),
     "nd_chebyshev_degree": ([_D, _D, ctypes.POINTER(_I)], _I),
     "nd_apply_sign": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
@@ -230,6 +233,21 @@ def nd_solve(ctx, xs, b, shifts, tol, maxit=100000, inner=ND_FP64):
     return info
 
 
+def nd_lowmodes_dynamic(ctx, l_min, l_max, kappa_target=1e-6, maxit=1000000):
+    """Low modes with l chosen in [l_min, l_max] by the largest relative gap, stopped at kappa_+- <=
+    kappa_target.  Returns (l, nu, rho, eval_Q2, info)."""
+    nu = (ctypes.c_double * l_max)()
+    rho = (ctypes.c_double * l_max)()
+    ev = (ctypes.c_double * (l_max + 1))()
+    lo = ctypes.c_int()
+    info = nd_lowmode_info()
+    st = lib().nd_lowmodes_dynamic(ctx, int(l_min), int(l_max), float(kappa_target), int(maxit), ctypes.byref(lo),
+                                   ctypes.cast(nu, _P), ctypes.cast(rho, _P), ctypes.cast(ev, _P), ctypes.byref(info))
+    _check(ctx, st, "nd_lowmodes_dynamic")
+    n = lo.value
+    return n, list(nu)[:n], list(rho)[:n], list(ev)[:n + 1], info
+
+
 def nd_lowmodes(ctx, l, tol=1e-12, maxit=100000):
     nu = (ctypes.c_double * l)()
     rho = (ctypes.c_double * l)()
@@ -305,6 +323,19 @@ def nd_apply_DN(ctx, out, inp, params):
     info = nd_dn_info()
     _check(ctx, lib().nd_apply_DN(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params), ctypes.byref(info)),
            "nd_apply_DN")
+    return info
+
+
+def nd_apply_Qhat(ctx, out, inp, prec):
+    """out_e = Qhat in_e on internal fields of precision prec (even halves only)."""
+    _check(ctx, lib().nd_apply_Qhat(ctx, _ptr(out), _ptr(inp), int(prec)), "nd_apply_Qhat")
+
+
+def nd_solve_Q2_eo(ctx, x, b, tol=1e-10, maxit=100000, inner=ND_FP64):
+    """x = (Q^2)^{-1} b via the even-odd Schur complement (canonical FP64 device tensors)."""
+    info = nd_solve_info()
+    _check(ctx, lib().nd_solve_Q2_eo(ctx, _ptr(_f64(x)), _ptr(_f64(b)), float(tol), int(maxit), int(inner),
+                                     ctypes.byref(info)), "nd_solve_Q2_eo")
     return info
 
 

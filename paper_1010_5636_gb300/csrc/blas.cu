@@ -15,7 +15,7 @@ __device__ __forceinline__ void site_ph(const Geom& g, int i, int* p, int* h) {
   *h = i - *p * g.Vh;
 }
 
-static int nblocks(const Geom& g) { return (2 * g.Vh + B_THREADS - 1) / B_THREADS; }
+static int nblocks(const Geom& g) { return (blas_sites(g) + B_THREADS - 1) / B_THREADS; }
 
 template <int P, bool REDUCE>
 __global__ void __launch_bounds__(B_THREADS) axpby_kernel(const Geom g, void* z, double a, const void* x, double b,
@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(B_THREADS) axpby_kernel(const Geom g, void* z,
   using T = typename Traits<P>::real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double red[1] = {0.0};
-  if (i < 2 * g.Vh) {
+  if (i < blas_sites(g)) {
     int p, h;
     site_ph(g, i, &p, &h);
     Spinor<T> vx, vy, vz;
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(B_THREADS) dot_kernel(const Geom g, const void
   using T = typename Traits<P>::real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double red[3] = {0.0, 0.0, 0.0};
-  if (i < 2 * g.Vh) {
+  if (i < blas_sites(g)) {
     int p, h;
     site_ph(g, i, &p, &h);
     Spinor<T> vx, vy;
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(B_THREADS) convert_kernel(const Geom g, void* 
   using TI = typename Traits<PI>::real;
   using TO = typename Traits<PO>::real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
+  if (i >= blas_sites(g)) return;
   int p, h;
   site_ph(g, i, &p, &h);
   Spinor<TI> v;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(B_THREADS) convert_kernel(const Geom g, void* 
 __global__ void __launch_bounds__(B_THREADS) g5_axpby_kernel(const Geom g, void* out, double c1, const void* x,
                                                               double c2, const void* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
+  if (i >= blas_sites(g)) return;
   int p, h;
   site_ph(g, i, &p, &h);
   Spinor<double> vx, vy, o;
@@ -109,6 +109,22 @@ __global__ void __launch_bounds__(B_THREADS) g5_axpby_kernel(const Geom g, void*
   SpinorIO<P64>::store(o, out, g.Vh, p, h);
 }
 
+template <int P>
+__global__ void __launch_bounds__(B_THREADS) g5_kernel(const Geom g, void* out, const void* in) {
+  using T = typename Traits<P>::real;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= blas_sites(g)) return;
+  int p, h;
+  site_ph(g, i, &p, &h);
+  Spinor<T> v;
+  SpinorIO<P>::load(v, in, g.Vh, p, h);
+#pragma unroll
+  for (int k = 2; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v.s[k][c] = -v.s[k][c];
+  SpinorIO<P>::store(v, out, g.Vh, p, h);
+}
+
 // (v_k, w) for K vectors; each thread reads w once and the K vectors' entries of its site.
 template <int K>
 __global__ void __launch_bounds__(B_THREADS) multidot_kernel(const Geom g, const char* base, size_t stride,
@@ -117,7 +133,7 @@ __global__ void __launch_bounds__(B_THREADS) multidot_kernel(const Geom g, const
   double red[2 * K];
 #pragma unroll
   for (int k = 0; k < 2 * K; ++k) red[k] = 0.0;
-  if (i < 2 * g.Vh) {
+  if (i < blas_sites(g)) {
     int p, h;
     site_ph(g, i, &p, &h);
     const double2* wb = reinterpret_cast<const double2*>(w) + (int64_t)p * 12 * g.Vh + h;
@@ -140,7 +156,7 @@ __global__ void __launch_bounds__(B_THREADS) lincomb_kernel(const Geom g, void* 
                                                              const char* base, size_t stride, int K,
                                                              const double* coef) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
+  if (i >= blas_sites(g)) return;
   int p, h;
   site_ph(g, i, &p, &h);
   const int64_t off = (int64_t)p * 12 * g.Vh + h;
@@ -208,6 +224,16 @@ cudaError_t blas_g5_axpby(const Geom& g, void* out, double c1, const void* x, do
   return cudaGetLastError();
 }
 
+cudaError_t blas_g5(const Geom& g, int prec, void* out, const void* in, cudaStream_t st) {
+  switch (prec) {
+    case P64: g5_kernel<P64><<<nblocks(g), B_THREADS, 0, st>>>(g, out, in); break;
+    case P32: g5_kernel<P32><<<nblocks(g), B_THREADS, 0, st>>>(g, out, in); break;
+    case P16: g5_kernel<P16><<<nblocks(g), B_THREADS, 0, st>>>(g, out, in); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t blas_multidot(const Geom& g, const void* base, size_t stride, int K, const void* w, ReduceSlot slot,
                           cudaStream_t st) {
   // results for chunks of 4 vectors; each chunk writes 8 doubles at slot.result + 8 * chunk
@@ -249,7 +275,7 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t x) {
 
 __global__ void random_kernel(const Geom g, void* out, uint64_t seed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
+  if (i >= blas_sites(g)) return;
   double2* o = reinterpret_cast<double2*>(out);
   const int p = i >= g.Vh ? 1 : 0, h = i - p * g.Vh;
   for (int c = 0; c < 12; ++c) {

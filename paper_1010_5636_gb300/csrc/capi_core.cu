@@ -110,6 +110,7 @@ nd_status nd_create(nd_ctx** out, const int dims[4], int antiperiodic_t, double 
   g.stride[0] = dims[3] * dims[2] * dims[1];
   g.Vh = (int)c->Vh;
   g.apbc = antiperiodic_t ? 1 : 0;
+  g.even_only = 0;
   c->max_blocks = (int)((V + 15) / 16) + 1024;  // >= blocks of any reducing launch (64 sites per block at least)
   bool ok = cudaMalloc(&c->red_partials, sizeof(double) * 8 * c->max_blocks) == cudaSuccess &&
             cudaMalloc(&c->red_counter, sizeof(unsigned) * 16) == cudaSuccess &&

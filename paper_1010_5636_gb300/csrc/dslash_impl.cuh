@@ -121,11 +121,12 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
   const double a_d = BASE == Q_CGUPDATE ? A.cgs[CG_ASCALE] : A.a;
   const double b_d = BASE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
   const T diag = (T)A.diag, ca = (T)a_d, cb = (T)b_d;
+  const T ca_lo = A.no_g5 ? ca : -ca;  // factor of the lower two spins: gamma5 = diag(1, 1, -1, -1)
   const bool read_diag = REDUCE || A.diag != 0.0;
   constexpr bool IN_PLACE = BASE == Q_CGUPDATE || BASE == Q_XPAY2 || BASE == Q_XPAY3;
   Spinor<T> d, y, z, w;
   if (act) {
-    if (read_diag) SpinorIO<P>::load(d, A.in, g.Vh, p, h);
+    if (read_diag) SpinorIO<P>::load(d, A.din ? A.din : A.in, g.Vh, p, h);
     if (BASE != Q_PLAIN || A.y) SpinorIO<P>::load(y, A.y, g.Vh, p, h);
     if (BASE == Q_CGUPDATE) SpinorIO<P>::load(z, A.out, g.Vh, p, h);
     if (BASE == Q_XPAY2 || BASE == Q_XPAY3) SpinorIO<P>::load(z, A.z, g.Vh, p, h);
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
       for (int c = 0; c < 3; ++c) {
         cx<T> v = (T)(-0.5) * acc.s[a][c];
         if (read_diag) v = v + diag * d.s[a][c];
-        v = (a < 2 ? ca : -ca) * v;  // gamma5 = diag(1, 1, -1, -1)
+        v = (a < 2 ? ca : ca_lo) * v;
         res.s[a][c] = v;
       }
     if (BASE == Q_PLAIN) {

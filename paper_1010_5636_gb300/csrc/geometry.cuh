@@ -17,7 +17,12 @@ struct Geom {
   int stride[4];   // lex strides: L1*L2*L3, L2*L3, L3, 1
   int Vh;          // sites per parity
   int apbc;        // 1: antiperiodic in time
+  int even_only;   // BLAS-1 kernels: 1 = fields of the even sites only (parity 0), 0 = whole lattice
 };
+
+// Sites a BLAS-1 launch covers: parity 0 comes first in every field layout, so an even-site field
+// is the first half of a whole-lattice one.
+__host__ __device__ inline int blas_sites(const Geom& g) { return g.even_only ? g.Vh : 2 * g.Vh; }
 
 struct Site {
   int x[4];

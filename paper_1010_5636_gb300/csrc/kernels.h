@@ -60,7 +60,9 @@ struct QLaunch {
   void* out;
   const void* y;
   const void* z;  // Q_XPAY2 and Q_XPAY3
-  const void* w;  // Q_XPAY3 only
+  const void* w;    // Q_XPAY3 only
+  const void* din;  // field the diagonal term reads (null: in)
+  int no_g5;        // 1: leave gamma5 out (out = a (diag * din - 1/2 hop(in)) + ...), i.e. D_W blocks
   double diag, a, b, c, d;
   int parity0, nsites;
   ReduceSlot slot;
@@ -125,6 +127,8 @@ cudaError_t blas_axpby(const Geom& g, int prec, void* z, double a, const void* x
 cudaError_t blas_dot(const Geom& g, int prec, const void* x, const void* y, ReduceSlot slot, cudaStream_t st);
 // out (prec_out) = in (prec_in); out may not alias in unless the precisions match
 cudaError_t blas_convert(const Geom& g, int prec_out, void* out, int prec_in, const void* in, cudaStream_t st);
+// out = gamma5 in (any precision; out may alias in)
+cudaError_t blas_g5(const Geom& g, int prec, void* out, const void* in, cudaStream_t st);
 // out = c1 x + c2 gamma5 y  (FP64 fields)
 cudaError_t blas_g5_axpby(const Geom& g, void* out, double c1, const void* x, double c2, const void* y,
                           cudaStream_t st);

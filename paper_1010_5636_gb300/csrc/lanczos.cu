@@ -342,6 +342,23 @@ nd_status rayleigh_ritz_q2(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size
 
 }  // namespace nd
 
+// One step of the filtered subspace iteration on the block X (k FP64 fields): filter every vector
+// with T_d(L(Q^2)) damping [lo, hi], lo = the largest Ritz value of the block, then re-orthonormalise
+// and Rayleigh-Ritz project.  FP32 filtering reaches residuals of about 1e-7 lambda_max; once the
+// worst wanted residual is below 1e-6 lambda_max the filter runs in FP64.
+nd_status filter_step(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size_t fs, double hi, double worst,
+                      std::vector<double>& theta, std::vector<double>& res, int* apps) {
+  const double lo = std::min(theta[k - 1], 0.5 * hi);
+  const int prec = (c->links[1] && worst > 1e-6 * hi) ? 1 : 0;
+  const int deg = prec == 1 ? 100 : 40;
+  for (int j = 0; j < k; ++j) ND_TRY(cheb_filter(c, prec, X + j * fs, deg, lo, hi));
+  *apps += k * deg;
+  ND_TRY(orthonormalise(c, X, k, fs));
+  ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
+  *apps += k;
+  return ND_OK;
+}
+
 // Low modes by Chebyshev-filtered subspace iteration on Q^2: a block of k = l+1+buffer FP64
 // vectors is filtered with T_d(L(Q^2)) (damping [lo, lambda_max], lo = the largest Ritz value
 // of the block), re-orthonormalised in FP64 and Rayleigh-Ritz projected with FP64 Q^2.  The
@@ -384,19 +401,10 @@ extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double
       break;
     }
     if (apps >= maxit) break;
-    const double lo = std::min(theta[k - 1], 0.5 * hi);
-    // FP32 filtering reaches residuals of about 1e-7 lambda_max; below 1e-6 lambda_max the
-    // filter switches to FP64 (needed only when tol asks for more than FP32 can give)
-    const int prec = (c->links[1] && worst > 1e-6 * hi) ? 1 : 0;
-    const int deg = prec == 1 ? 100 : 40;
     if (trace)
-      std::fprintf(stderr, "nd_lowmodes: it %d apps %d filter fp%d lo %.6g hi %.6g theta0 %.6g theta_l %.6g worst %.3g nconv %d\n",
-                   it, apps, prec == 0 ? 64 : 32, lo, hi, theta[0], theta[l], worst, nconv);
-    for (int j = 0; j < k; ++j) ND_TRY(cheb_filter(c, prec, X + j * fs, deg, lo, hi));
-    apps += k * deg;
-    ND_TRY(orthonormalise(c, X, k, fs));
-    ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
-    apps += k;
+      std::fprintf(stderr, "nd_lowmodes: it %d apps %d hi %.6g theta0 %.6g theta_l %.6g worst %.3g nconv %d\n", it,
+                   apps, hi, theta[0], theta[l], worst, nconv);
+    ND_TRY(filter_step(c, X, AX, Y, k, fs, hi, worst, theta, res, &apps));
     lam_max = std::max(lam_max, theta[k - 1]);
   }
   // keep the workspace registry pointing at the right buffers after the swaps
@@ -478,5 +486,98 @@ extern "C" nd_status nd_get_lowmodes(nd_ctx* c, double* evecs, double* nu) {
     if (nu) nu[k] = c->nu[k];
   }
   ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  return ND_OK;
+}
+
+// Low modes with the number l chosen dynamically and kappa_+- driving the stopping (Sec. 2.3).
+// The block iteration above runs for l_max + 1 wanted modes.  After each step the candidate l in
+// [l_min, l_max] with the largest relative gap (sqrt(theta_{l+1}) - sqrt(theta_l)) / sqrt(theta_{l+1})
+// between the last kept and the first remaining Ritz value of Q^2 is taken (smallest l on ties), so
+// that the spectral distance d_k entering kappa is not accidentally small.  Once the l + 1 lowest
+// Q^2 residuals are below 1e-4 lambda_max, the Rayleigh-Ritz pairs of Q on the first l vectors give
+// rho_k and kappa_+- (d_k as in nd_lowmodes, lambda_{l+1} ~ theta_{l+1}); the iteration stops when
+// both kappas are at most kappa_target.
+extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
+                                         double* nu_out, double* rho_out, double* evq2_out, nd_lowmode_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (l_min < 1 || l_max < l_min || l_max > 64 || !(kappa_target > 0) || maxit < 1)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_lowmodes_dynamic: need 1 <= l_min <= l_max <= 64, kappa_target > 0");
+  if (!c->links[0]) return fail(c, ND_ERR_STATE, "nd_lowmodes_dynamic: FP64 links not set");
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  double lam_max;
+  ND_TRY(lambda_max_estimate(c, 40, &lam_max));
+  const double hi = 1.01 * lam_max;
+  const int nwant = l_max + 1;
+  const int k = std::min(std::max(nwant + 8, 2 * nwant), 130);
+  char* X = static_cast<char*>(field(c, "cf_X", 0, k));
+  char* AX = static_cast<char*>(field(c, "cf_AX", 0, k));
+  char* Y = static_cast<char*>(field(c, "cf_Y", 0, k));
+  char* Z = static_cast<char*>(field(c, "cf_Z", 0, l_max));
+  if (!X || !AX || !Y || !Z) return fail(c, ND_ERR_OOM, "nd_lowmodes_dynamic: workspace");
+  for (int j = 0; j < k; ++j) ND_TRY_CUDA(c, blas_random(c->g, X + j * fs, 777 + 7919ull * j, c->stream));
+  ND_TRY(orthonormalise(c, X, k, fs));
+  std::vector<double> theta, res, nu, rho;
+  ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
+  int apps = k, l = l_min;
+  double kp = INFINITY, km = INFINITY;
+  const bool trace = std::getenv("ND_TRACE") != nullptr;
+  bool converged = false;
+  for (int it = 0; it < 1000; ++it) {
+    // the candidate with the largest relative gap
+    double best = -1.0;
+    for (int j = l_min; j <= l_max; ++j) {
+      const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
+      const double g = b > 0 ? (b - a) / b : 0.0;
+      if (g > best) {
+        best = g;
+        l = j;
+      }
+    }
+    double worst = 0.0;
+    for (int i = 0; i <= l; ++i) worst = std::max(worst, res[i]);
+    if (worst <= 1e-4 * hi) {
+      ND_TRY_CUDA(c, cudaMemcpyAsync(Z, X, fs * l, cudaMemcpyDeviceToDevice, c->stream));
+      ND_TRY(ritz_of_Q(c, Z, l, nu, rho));
+      apps += (l + 1) / 2;
+      kappas(nu, rho, theta[l], &kp, &km);
+      if (trace)
+        std::fprintf(stderr, "nd_lowmodes_dynamic: it %d apps %d l %d gap %.3g worst %.3g kappa+ %.3g kappa- %.3g\n", it,
+                     apps, l, best, worst, kp, km);
+      if (kp <= kappa_target && km <= kappa_target) {
+        converged = true;
+        break;
+      }
+    }
+    if (apps >= maxit) break;
+    ND_TRY(filter_step(c, X, AX, Y, k, fs, hi, worst, theta, res, &apps));
+    lam_max = std::max(lam_max, theta[k - 1]);
+  }
+  c->ws["cf_X"].first = X;
+  c->ws["cf_AX"].first = AX;
+  c->ws["cf_Y"].first = Y;
+  if (!converged)
+    return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes_dynamic: kappa target not reached within maxit Q^2 applications");
+  c->lam_next = theta[l];
+  ND_TRY(store_modes(c, Z, l));
+  c->nu = nu;
+  c->rho = rho;
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (l_out) *l_out = l;
+  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
+  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
+  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
+  if (info) {
+    info->l = l;
+    info->iters = apps;
+    info->lambda_max = lam_max;
+    info->lambda_next = c->lam_next;
+    info->kappa_plus = kp;
+    info->kappa_minus = km;
+    info->max_rho = *std::max_element(rho.begin(), rho.end());
+    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  c->lam_max = lam_max;
   return ND_OK;
 }

@@ -1,5 +1,6 @@
 """Pins of the oracle's ARPACK low-mode path against dense LAPACK diagonalisation."""
 import numpy as np
+import pytest
 
 import synth
 from oracle import lowmodes
@@ -20,3 +21,18 @@ def test_arpack_matches_dense():
     Pd = np.einsum("kx,ky->xy", de["u"].reshape(l, -1), de["u"].reshape(l, -1).conj())
     assert np.linalg.norm(Pa - Pd, 2) < 1e-8
     assert np.max(ar["rho"]) < 1e-8
+
+
+def test_choose_l_rule():
+    # eigenvalues of Q^2 with one clear relative gap after the 5th mode
+    ev = np.array([0.01, 0.011, 0.0112, 0.0113, 0.0115, 0.05, 0.051, 0.052, 0.06, 0.061])
+    assert lowmodes.choose_l(ev, 2, 8) == 5
+    assert lowmodes.choose_l(ev * 37.0, 2, 8) == 5  # scale invariant
+    assert lowmodes.choose_l(ev, 6, 8) == 8  # 0.052 -> 0.06 is the largest gap in that window
+    assert lowmodes.choose_l(ev, 3, 3) == 3
+    # ties go to the smaller l
+    assert lowmodes.choose_l(np.array([1.0, 4.0, 16.0, 64.0]), 1, 3) == 1
+    with pytest.raises(ValueError):
+        lowmodes.choose_l(ev, 0, 3)
+    with pytest.raises(ValueError):
+        lowmodes.choose_l(ev, 2, 10)
