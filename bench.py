@@ -411,6 +411,30 @@ def dn_phase(nd, torch, reps):
     t = time.perf_counter() - t0
     res["propagator"] = {"s": round(t, 3), "outer_iters": pinf.iters, "sign_krylov_iters": pinf.sign_iters,
                          "resid": pinf.resid, "m_q": 0.1, "inner": "mixed_fp32, sign to 1e-12"}
+    # the paper's error control: l chosen in [12, 40] by the largest relative gap, modes refined until
+    # kappa_+- <= 1e-4; then the mixed FP32 D_N with those modes (eps from the chosen lambda_{l+1})
+    t0 = time.perf_counter()
+    ld, _, _, _, lid = nd.nd_lowmodes_dynamic(ctx, 12, 40, 1e-4, 20000000)
+    t_dyn = time.perf_counter() - t0
+    kmax = max(lid.kappa_plus, lid.kappa_minus)
+    kk = kmax * (1 + 2 * kmax)
+    dyn = {"l": ld, "s": round(t_dyn, 3), "q2_applications": lid.iters, "kappa_plus": lid.kappa_plus,
+           "kappa_minus": lid.kappa_minus, "projector_bound": kk / (1 - 2 * kk) if 2 * kk < 1 else None,
+           "lambda_next": lid.lambda_next, "lambda_max": lid.lambda_max}
+    p = nd.dn_params(20, 0.0, 0.0, 1e-10, 200000, 1, 0.0, False)
+    o = torch.empty_like(eta)
+    nd.nd_apply_DN(ctx, o, eta, p)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        info = nd.nd_apply_DN(ctx, o, eta, p)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    t = float(np.median(ts))
+    dyn["mixed_fp32"] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "eps": info.eps,
+                         "krylov_iters": info.iters, "refinement_sweeps": info.outer}
+    res["dynamic_l"] = dyn
     base = outs["fp64"]
     for name in ("mixed_fp32", "mixed_fp16", "poly_fp64", "poly_fp32"):
         res[name]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs[name] - base) /

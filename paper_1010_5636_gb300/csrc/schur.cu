@@ -181,13 +181,15 @@ extern "C" nd_status nd_solve_Q2_eo(nd_ctx* c, double* x_out, const double* b_in
     }
     prev = rel;
     const double tin = std::max(0.1 * tol / rel, floor_in);
-    ND_TRY_CUDA(c, blas_g5_axpby(c->g, r, 0.0, r, 1.0, r, c->stream));  // r <- gamma5 r
+    // r <- gamma5 r / ||r||: unit norm before the inner precision (no subnormal products there)
+    const double rn = rel * std::sqrt(bn2);
+    ND_TRY_CUDA(c, blas_g5_axpby(c->g, r, 0.0, r, 1.0 / rn, r, c->stream));
     ND_TRY_CUDA(c, blas_convert(c->g, ps, vs, 0, r, c->stream));
     ND_TRY(dw_inverse(c, ps, ys, vs, tin, maxit, &inf.iters));
     ND_TRY_CUDA(c, blas_g5(c->g, ps, ys, ys, c->stream));
     ND_TRY(dw_inverse(c, ps, es, ys, tin, maxit, &inf.iters));
     ND_TRY_CUDA(c, blas_convert(c->g, 0, r, ps, es, c->stream));
-    ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0, x, 1.0, r, false, slot(c, nullptr), c->stream));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0, x, rn, r, false, slot(c, nullptr), c->stream));
     ND_TRY(residual64(c, r, b, x, 0.0, 1.0, bn2, &rel));
     ++inf.outer;
   }

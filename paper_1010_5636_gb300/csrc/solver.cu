@@ -369,7 +369,23 @@ nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double si
   double* res = c->red_scratch + 8;
   ND_TRY(q_apply(c, 0, t, x));
   ND_TRY(q_apply(c, 0, r, t, ascale, sigma, x));  // r = (ascale Q^2 + sigma) x
-  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, true, slot(c, res), c->stream));
+  const bool project = c->deflated_solve && c->nlow > 0;
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, !project, slot(c, res), c->stream));
+  if (project) {
+    // r <- (1 - P) r, P the projector on the context's low modes: the deflated system lives on the
+    // complement, where A >= lambda_{l+1}/lambda_max + sigma keeps the corrections well conditioned
+    const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+    const int l = c->nlow;
+    double* cdev = static_cast<double*>(workspace(c, "res_c", sizeof(double) * 4 * 64));
+    if (!cdev) return fail(c, ND_ERR_OOM, "residual: workspace");
+    std::vector<double> ck(2 * l);
+    ND_TRY_CUDA(c, blas_multidot(c->g, c->evecs, fs, l, r, slot(c, cdev), c->stream));
+    ND_TRY(read_back(c, cdev, ck.data(), 2 * l));
+    for (double& v : ck) v = -v;
+    ND_TRY_CUDA(c, cudaMemcpyAsync(cdev + 2 * 64, ck.data(), sizeof(double) * 2 * l, cudaMemcpyHostToDevice, c->stream));
+    ND_TRY_CUDA(c, blas_lincomb(c->g, r, 1.0, r, c->evecs, fs, l, cdev + 2 * 64, c->stream));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, r, 0.0, nullptr, true, slot(c, res), c->stream));
+  }
   double h;
   ND_TRY(read_back(c, res, &h, 1));
   *rel = std::sqrt(h / bnorm2);
@@ -392,7 +408,12 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   char* x32 = static_cast<char*>(field(c, "mx_x32", 1, n));
   void* r64 = field(c, "mx_r64", 0);
   if (!bS || !x32 || !r64) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
-  ND_TRY_CUDA(c, blas_convert(c->g, ps, bS, 0, b64, c->stream));
+  // Every field handed to the sloppy precision is scaled to unit norm first (and its solution
+  // scaled back in FP64): a source or residual of small norm would otherwise reach FP32 products
+  // and squared norms in the subnormal range, where the Krylov scalars lose their digits.
+  const double bnorm = std::sqrt(bnorm2);
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r64, 1.0 / bnorm, b64, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+  ND_TRY_CUDA(c, blas_convert(c->g, ps, bS, 0, r64, c->stream));
   std::vector<double> tol_s(n);
   for (int l = 0; l < n; ++l) tol_s[l] = std::max(tol[l], floor_s);
   const bool trace = std::getenv("ND_TRACE") != nullptr;
@@ -419,8 +440,16 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   char* R32 = static_cast<char*>(field(c, "mx_R32", 1, n));
   char* E32 = static_cast<char*>(field(c, "mx_E32", 1, n));
   if (!X64 || !R32 || !E32) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
-  for (int l = 0; l < n; ++l) ND_TRY_CUDA(c, blas_convert(c->g, 0, X64 + l * f64, 1, x32 + l * f32, c->stream));
+  for (int l = 0; l < n; ++l) {
+    ND_TRY_CUDA(c, blas_convert(c->g, 0, X64 + l * f64, 1, x32 + l * f32, c->stream));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, bnorm, X64 + l * f64, 0.0, nullptr, false, slot(c, nullptr),
+                              c->stream));
+  }
   std::vector<double> rel(n, 1.0), first(n, -1.0), prev(n, 1e300);
+  // per-shift reduction asked of a correction solve; raised tenfold (up to 1e-2) after a correction
+  // that ran into its iteration cap: an FP32 CG resolves relative reductions down to about
+  // u_32 kappa, which the lowest shifts of a deflated system only just clear
+  std::vector<double> tin(n, floor_in), rnorm(n, 1.0);
   std::vector<int> outer(n, 0), flat(n, 0);
   std::vector<bool> done(n, false);
   for (int sweep = 0;; ++sweep) {
@@ -459,16 +488,24 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
                       rel[l], tol[l]);
         return fail(c, ND_ERR_NOT_CONVERGED, msg);
       }
+      // r64 / ||r64|| to FP32 (see above); the correction is scaled back by rnorm[l]
+      rnorm[l] = rel[l] * bnorm;
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, r64, 1.0 / rnorm[l], r64, 0.0, nullptr, false, slot(c, nullptr), c->stream));
       ND_TRY_CUDA(c, blas_convert(c->g, 1, R32 + pend.size() * f32, 0, r64, c->stream));
       pend.push_back(l);
       sig_p.push_back(sigma[l]);
-      tol_p.push_back(std::max(0.3 * tol[l] / rel[l], floor_in));
+      tol_p.push_back(std::max(0.3 * tol[l] / rel[l], tin[l]));
     }
     if (pend.empty()) break;
     if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
     std::vector<int> it;
     auto tb = now();
-    s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, maxit, &it);
+    // a correction asks for a modest reduction; needing many more iterations than the sloppy pass
+    // means it is stuck on rounding, and the next FP64 residual decides
+    // (rounded up to a power of two: the captured graph is keyed by the limit)
+    int cap = 128;
+    while (cap < 8 * st->iters + 100) cap *= 2;
+    s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, std::min(maxit, cap), &it);
     if (s != ND_OK) return s;
     if (trace) {
       const double dt = ms_since(tb);
@@ -480,9 +517,10 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
     for (size_t k = 0; k < pend.size(); ++k) {
       const int l = pend[k];
       st->sloppy_iters += it[k];
+      if (it[k] >= std::min(maxit, cap)) tin[l] = std::min(10.0 * tin[l], 1e-2);
       ++outer[l];
       ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, E32 + k * f32, c->stream));
-      ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, 1.0, X64 + l * f64, 1.0, r64, false, slot(c, nullptr),
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, 1.0, X64 + l * f64, rnorm[l], r64, false, slot(c, nullptr),
                                 c->stream));
     }
     if (trace) t_upd += ms_since(tu);
