@@ -122,33 +122,51 @@ def dist_setup(args):
     return world, rank, local
 
 
+def _reduce_device():
+    """NCCL reduces CUDA tensors, gloo host tensors."""
+    import torch
+    import torch.distributed as dist
+    if dist.get_backend() == "nccl":
+        return torch.device("cuda", torch.cuda.current_device())
+    return torch.device("cpu")
+
+
 def barrier_sync(world):
     import torch
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
+
+
+def _all_reduce(x, world, op):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=_reduce_device())
+    dist.all_reduce(t, op=op)
+    return float(t.item())
 
 
 def max_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    return x if world == 1 else _all_reduce(x, world, dist.ReduceOp.MAX)
 
 
 def sum_over_ranks(x, world):
-    if world == 1:
-        return x
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([float(x)], device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return x if world == 1 else _all_reduce(x, world, dist.ReduceOp.SUM)
+
+
+def whole_job_rate(units, ms, world):
+    """Units of all ranks per second of the slowest rank (replicas: each rank times its own
+    independent work).  Returns (rate, slowest ms)."""
+    ms_max = max_over_ranks(ms, world)
+    return sum_over_ranks(units, world) / (ms_max * 1e-3), ms_max
 
 
 def oracle_baseline(seconds_target=15.0):
@@ -204,7 +222,8 @@ def reference_arm(args):
     el = time.perf_counter() - t0
     rate = steps * V / el
     val = rate * site_bytes(1, RECON) / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s", "n_gpus": 1, "steps": steps,
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "GB/s",
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps,
             "warmup": warm, "ms_per_step": 1e3 * el / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"even-odd Dslash on {DIMS[1]}^3x{DIMS[0]} (oracle: FP64 Q, both parities)",
@@ -263,11 +282,10 @@ def dslash_phase(nd, torch, steps, warm, world, clocks):
             ev[2 * k + 1][1].record(stream)
         t1.record(stream)
         barrier_sync(world)
-    total_ms = t0.elapsed_time(t1)
     launch_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
-    total_ms = max_over_ranks(total_ms, world)
     bytes_step = V * site_bytes(prec, RECON)
-    gbs = sum_over_ranks(bytes_step * steps, world) / (total_ms * 1e-3) / 1e9
+    rate, total_ms = whole_job_rate(bytes_step * steps, t0.elapsed_time(t1), world)
+    gbs = rate / 1e9
     avg_launch = sum(launch_ms) / len(launch_ms)
     per_launch_bytes = bytes_step / 2
     # end to end through the public API with host buffers: pinned canonical FP64 input copied in,
@@ -294,8 +312,8 @@ def dslash_phase(nd, torch, steps, warm, world, clocks):
         e2e_step()
     e1.record(stream)
     barrier_sync(world)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e_gbs = sum_over_ranks(bytes_step * steps, world) / (e2e_ms * 1e-3) / 1e9
+    rate, e2e_ms = whole_job_rate(bytes_step * steps, e0.elapsed_time(e1), world)
+    e2e_gbs = rate / 1e9
     nbytes_io = psi_pin.numel() * psi_pin.element_size()
     nd.nd_destroy(ctx)
     return {"total_ms": total_ms, "gbs": gbs, "avg_launch_ms": avg_launch, "per_launch_bytes": per_launch_bytes,
