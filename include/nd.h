@@ -278,7 +278,8 @@ nd_status nd_apply_DN(nd_ctx* ctx, double* out_dev, const double* in_dev, const 
 /* ---------------------------------------------------------------- propagators */
 
 typedef struct {
-  int iters;           /* outer CG iterations (one sign(Q) application each), both chiralities */
+  int iters;           /* CG iterations on H (one sign(Q) application each), all passes and chiralities */
+  int outer;           /* defect-correction passes on D_N^m x = b */
   int sign_iters;      /* Krylov iterations (Zolotarev) or Clenshaw iterations (Chebyshev) of all sign(Q) applications */
   double resid;        /* true relative residual ||b - D_N^m x|| / ||b|| (with the same approximate sign(Q)) */
   double time_ms;
@@ -287,8 +288,10 @@ typedef struct {
 /* x = (D_N^m)^{-1} b for the massive overlap operator D_N^m = (1 - abar m_q/2) D_N + m_q (Sec. 2.2).
  * D_N^m is normal for a hermitian sign(Q), and H = D_N^m D_N^m^dagger commutes with gamma5; each
  * chirality of b is solved by CG on H (one sign(Q) application per iteration, approximation,
- * deflation and inner precision as in p) to ||P_c b - H y_c|| <= tol ||P_c b||, and
- * x = gamma5 D_N^m gamma5 y.  p->left_only must be 0 (the left-only form is not hermitian).
+ * deflation and inner precision as in p), and x = gamma5 D_N^m gamma5 y.  An outer defect
+ * correction on D_N^m x = b (two more sign(Q) applications per pass) stops at
+ * ||b - D_N^m x|| <= tol ||b||, with D_N^m built from the same approximate sign(Q), whose sign^2 = 1
+ * holds only to its accuracy.  p->left_only must be 0 (the left-only form is not hermitian).
  * b_dev, x_dev: canonical FP64 device spinors (may not overlap).  ND_ERR_NOT_CONVERGED after
  * maxit iterations of either chirality (x holds the last iterate); m_q > 0 keeps H >= m_q^2. */
 nd_status nd_propagator(nd_ctx* ctx, double* x_dev, const double* b_dev, const nd_dn_params* p, double tol,

@@ -53,8 +53,8 @@ class nd_dn_info(ctypes.Structure):
 
 
 class nd_prop_info(ctypes.Structure):
-    _fields_ = [("iters", ctypes.c_int), ("sign_iters", ctypes.c_int), ("resid", ctypes.c_double),
-                ("time_ms", ctypes.c_double)]
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("sign_iters", ctypes.c_int),
+                ("resid", ctypes.c_double), ("time_ms", ctypes.c_double)]
 
 
 _P, _I, _D, _L = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64

@@ -43,9 +43,6 @@ struct nd_ctx {
   std::map<std::string, std::pair<void*, size_t>> ws;
   // low modes: FP64 internal fields [l], nu, rho
   int nlow = 0;
-  // set while sign(Q) runs its two-sided deflated solve: the mixed-precision refinement then
-  // measures and corrects residuals on the complement of the low modes only
-  bool deflated_solve = false;
   void* evecs = nullptr;
   size_t evecs_cap = 0;
   std::vector<double> nu, rho;

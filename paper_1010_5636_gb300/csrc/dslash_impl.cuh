@@ -207,16 +207,23 @@ static cudaError_t launch_q5(const Geom& g, const QLaunch& L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-// Block shapes.  One warp per site: FP32 and FP16 run 64-thread blocks capped at 128 registers
-// (8 blocks per SM); on 64x32^3 this beats 256-thread blocks by 20-25 % (more independent
-// blocks in flight per SM, smaller tail).  FP64 is FP64-ALU bound and keeps 256 threads.
-// Split kernels combine warps through shared memory and use 256-thread blocks.
+// Block shapes.  One warp per site: FP32 and FP16 run 64-thread blocks; on 64x32^3 these beat
+// 256-thread blocks by 20-30 % (more independent blocks in flight per SM, smaller tail).  The
+// register cap is 128 (8 blocks per SM) except for FP32 18-real links, where 6 blocks per SM
+// (170 registers) is 7 % faster (sweep of 8/6/5/4 blocks per SM: FP32-12 6002/5783/5782/5780 GB/s,
+// FP32-18 6329/6752/6753/5967 GB/s).  FP64 is FP64-ALU bound and keeps 256 threads.  Split
+// kernels combine warps through shared memory and use 256-thread blocks.
+template <int P, int R>
+constexpr int q_min_blocks() {
+  return (P == P32 && R == 18) ? 6 : 8;
+}
+
 template <int P, int R, int MODE, bool REDUCE>
 static cudaError_t launch_q4(const Geom& g, const QLaunch& L, cudaStream_t st) {
   switch (L.split) {
     case 1:
       if (P == P64 || L.threads == 256) return launch_q5<P, R, MODE, REDUCE, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, MODE, REDUCE, 1, 64, 8>(g, L, st);
+      return launch_q5<P, R, MODE, REDUCE, 1, 64, q_min_blocks<P, R>()>(g, L, st);
     case 2: return launch_q5<P, R, MODE, REDUCE, 2, 256, 1>(g, L, st);
     case 4: return launch_q5<P, R, MODE, REDUCE, 4, 256, 1>(g, L, st);
   }
@@ -239,7 +246,7 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
     case Q_MRHS:
       if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64 || L.threads == 256) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, Q_MRHS, false, 1, 64, 8>(g, L, st);
+      return launch_q5<P, R, Q_MRHS, false, 1, 64, q_min_blocks<P, R>()>(g, L, st);
     case Q_BPLAIN:
       if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64) return launch_q5<P, R, Q_BPLAIN, true, 1, 256, 1>(g, L, st);

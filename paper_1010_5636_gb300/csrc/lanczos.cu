@@ -496,7 +496,8 @@ extern "C" nd_status nd_get_lowmodes(nd_ctx* c, double* evecs, double* nu) {
 // that the spectral distance d_k entering kappa is not accidentally small.  Once the l + 1 lowest
 // Q^2 residuals are below 1e-4 lambda_max, the Rayleigh-Ritz pairs of Q on the first l vectors give
 // rho_k and kappa_+- (d_k as in nd_lowmodes, lambda_{l+1} ~ theta_{l+1}); the iteration stops when
-// both kappas are at most kappa_target.
+// both kappas are at most kappa_target.  Once all candidates' Ritz values have settled, l is
+// fixed and the block shrinks to the vectors needed for the kept modes.
 extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
                                          double* nu_out, double* rho_out, double* evq2_out, nd_lowmode_info* info) {
   if (!c) return ND_ERR_INVALID_ARG;
@@ -524,15 +525,31 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
   double kp = INFINITY, km = INFINITY;
   const bool trace = std::getenv("ND_TRACE") != nullptr;
   bool converged = false;
+  bool fixed = false;
+  int kb = k;  // current block size
+  double best = -1.0;
   for (int it = 0; it < 1000; ++it) {
-    // the candidate with the largest relative gap
-    double best = -1.0;
-    for (int j = l_min; j <= l_max; ++j) {
-      const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
-      const double g = b > 0 ? (b - a) / b : 0.0;
-      if (g > best) {
-        best = g;
-        l = j;
+    if (!fixed) {
+      // the candidate with the largest relative gap
+      best = -1.0;
+      for (int j = l_min; j <= l_max; ++j) {
+        const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
+        const double g = b > 0 ? (b - a) / b : 0.0;
+        if (g > best) {
+          best = g;
+          l = j;
+        }
+      }
+      // once every candidate's Ritz value is settled (residual <= 1e-3 lambda_max bounds its error
+      // by ~1e-6 lambda_max^2 / gap), l is fixed and the block shrinks to the lowest
+      // max(l + 9, 2 (l + 1)) Ritz vectors: the rest of the work only refines the kept modes
+      double worst_all = 0.0;
+      for (int i = 0; i <= l_max; ++i) worst_all = std::max(worst_all, res[i]);
+      if (worst_all <= 1e-3 * hi) {
+        fixed = true;
+        kb = std::min(kb, std::max(l + 9, 2 * (l + 1)));
+        theta.resize(kb);
+        res.resize(kb);
       }
     }
     double worst = 0.0;
@@ -551,8 +568,8 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
       }
     }
     if (apps >= maxit) break;
-    ND_TRY(filter_step(c, X, AX, Y, k, fs, hi, worst, theta, res, &apps));
-    lam_max = std::max(lam_max, theta[k - 1]);
+    ND_TRY(filter_step(c, X, AX, Y, kb, fs, hi, worst, theta, res, &apps));
+    if (!fixed) lam_max = std::max(lam_max, theta[kb - 1]);
   }
   c->ws["cf_X"].first = X;
   c->ws["cf_AX"].first = AX;

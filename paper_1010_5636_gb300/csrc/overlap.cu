@@ -161,9 +161,7 @@ static nd_status sign_impl(nd_ctx* c, const double* in, const nd_dn_params* p, n
       ND_TRY_CUDA(c, blas_axpby(c->g, 0, y, 1.0, y, bw[k], x64, false, slot(c, nullptr), c->stream));
       return ND_OK;
     };
-    c->deflated_solve = two_sided;
     nd_status s = mixed_solve(c, (int)p->inner_prec, src, bn2, sigma, tol, ascale, p->maxit, &ms, sink);
-    c->deflated_solve = false;
     if (s != ND_OK) return s;
     inf.iters = ms.iters;
     inf.sloppy_iters = ms.sloppy_iters;

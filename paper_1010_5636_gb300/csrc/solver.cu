@@ -369,23 +369,7 @@ nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double si
   double* res = c->red_scratch + 8;
   ND_TRY(q_apply(c, 0, t, x));
   ND_TRY(q_apply(c, 0, r, t, ascale, sigma, x));  // r = (ascale Q^2 + sigma) x
-  const bool project = c->deflated_solve && c->nlow > 0;
-  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, !project, slot(c, res), c->stream));
-  if (project) {
-    // r <- (1 - P) r, P the projector on the context's low modes: the deflated system lives on the
-    // complement, where A >= lambda_{l+1}/lambda_max + sigma keeps the corrections well conditioned
-    const size_t fs = (size_t)spinor_bytes(0, c->Vh);
-    const int l = c->nlow;
-    double* cdev = static_cast<double*>(workspace(c, "res_c", sizeof(double) * 4 * 64));
-    if (!cdev) return fail(c, ND_ERR_OOM, "residual: workspace");
-    std::vector<double> ck(2 * l);
-    ND_TRY_CUDA(c, blas_multidot(c->g, c->evecs, fs, l, r, slot(c, cdev), c->stream));
-    ND_TRY(read_back(c, cdev, ck.data(), 2 * l));
-    for (double& v : ck) v = -v;
-    ND_TRY_CUDA(c, cudaMemcpyAsync(cdev + 2 * 64, ck.data(), sizeof(double) * 2 * l, cudaMemcpyHostToDevice, c->stream));
-    ND_TRY_CUDA(c, blas_lincomb(c->g, r, 1.0, r, c->evecs, fs, l, cdev + 2 * 64, c->stream));
-    ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, r, 0.0, nullptr, true, slot(c, res), c->stream));
-  }
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, true, slot(c, res), c->stream));
   double h;
   ND_TRY(read_back(c, res, &h, 1));
   *rel = std::sqrt(h / bnorm2);

@@ -121,3 +121,22 @@ def test_edge_cases(nd, cfg1):
         assert info.resid <= 5e-9
     finally:
         nd.nd_destroy(ctx)
+
+
+def test_inexact_sign_needs_outer_passes(nd, cfg1):
+    """With a sign(Q) accurate to ~1e-6 only (a low-degree polynomial), H = D D^dagger no longer holds
+    to the solve tolerance; the defect correction still brings ||b - D x|| below tol."""
+    import torch
+    dims, U, lm, lam_max, eps = cfg1
+    b = synth.spinor(dims, seed=12)
+    degree = chebyshev.degree_for(eps, 1e-6)
+    ctx = _ctx(nd, dims, U, lm)
+    try:
+        p = nd.dn_params(0, eps, lam_max, 1e-6, 1, 0, 0.1, False, approx=nd.ND_SIGN_CHEBYSHEV, degree=degree)
+        x = torch.empty_like(dev(b))
+        info = nd.nd_propagator(ctx, x, dev(b), p, tol=1e-10, maxit=5000)
+        print(f"degree {degree}: passes {info.outer}, CG iterations {info.iters}, resid {info.resid:.2e}")
+        assert info.resid <= 1e-10
+        assert info.outer >= 2
+    finally:
+        nd.nd_destroy(ctx)
