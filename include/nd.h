@@ -94,6 +94,12 @@ nd_status nd_set_links(nd_ctx* ctx, const double* U_dev, const int recon[3]);
 nd_status nd_pack_spinor(nd_ctx* ctx, void* internal_dev, const double* canon_dev, nd_prec prec, int nrhs);
 nd_status nd_unpack_spinor(nd_ctx* ctx, double* canon_dev, const void* internal_dev, nd_prec prec, int nrhs);
 
+/* The same two conversions for canonical fields in single precision ([V][4][3] complex64,
+ * interleaved FP32; half the host <-> device bytes of the FP64 form).  Packing to ND_FP64 widens
+ * exactly; unpacking from ND_FP64 rounds to nearest. */
+nd_status nd_pack_spinor_f32(nd_ctx* ctx, void* internal_dev, const float* canon_dev, nd_prec prec, int nrhs);
+nd_status nd_unpack_spinor_f32(nd_ctx* ctx, float* canon_dev, const void* internal_dev, nd_prec prec, int nrhs);
+
 /* Export the GPU's site tables: lex2eo_dev[V] (eo index of each lex site) and
  * nbr_dev[8][V] (eo index of the neighbour of eo site e in direction d = 2*mu + s,
  * s = 0 for x + mu, 1 for x - mu), both int32, device. */
@@ -204,6 +210,16 @@ nd_status nd_lowmodes(nd_ctx* ctx, int l, double tol, int maxit, double* nu, dou
  * ND_ERR_NOT_CONVERGED when maxit Q^2 applications do not reach the target. */
 nd_status nd_lowmodes_dynamic(nd_ctx* ctx, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
                               double* nu, double* rho, double* eval_Q2, nd_lowmode_info* info);
+
+/* The same choice of l and stopping rule with the paper's own minimiser (Sec. 2.3): l_max + 1
+ * vectors, each minimising the Ritz functional (x, Q^2 x) / (x, x) on the complement of the ones
+ * before it by nonlinear conjugate gradients (exact minimum on span{x, p} each step), then one
+ * Rayleigh-Ritz step of Q^2 on all of them; while kappa_+- > kappa_target the minimisation is
+ * repeated with a ten times smaller gradient tolerance (from 1e-4 lambda_max).  FP64 throughout.
+ * Converges one vector at a time: slow where the low spectrum is a dense band.  Outputs as
+ * nd_lowmodes_dynamic. */
+nd_status nd_lowmodes_ritz(nd_ctx* ctx, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
+                           double* nu, double* rho, double* eval_Q2, nd_lowmode_info* info);
 
 /* Replace the context's low modes by caller-provided orthonormal vectors (canonical FP64,
  * device, [l][V*12] complex) with their Q eigenvalues nu (host) and an estimate of

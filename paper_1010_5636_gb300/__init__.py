@@ -69,6 +69,8 @@ _SIGS = {
     "nd_set_links": ([_P, _P, _P], _I),
     "nd_pack_spinor": ([_P, _P, _P, _I, _I], _I),
     "nd_unpack_spinor": ([_P, _P, _P, _I, _I], _I),
+    "nd_pack_spinor_f32": ([_P, _P, _P, _I, _I], _I),
+    "nd_unpack_spinor_f32": ([_P, _P, _P, _I, _I], _I),
     "nd_eo_tables": ([_P, _P, _P], _I),
     "nd_apply_Q": ([_P, _P, _P, _I, _I], _I),
     "nd_apply_Q_parity": ([_P, _P, _P, _I, _I, _D], _I),
@@ -84,6 +86,7 @@ _SIGS = {
     "nd_chebyshev": ([_I, _D, _P, ctypes.POINTER(_D)], _I),
     "nd_apply_Qhat": ([_P, _P, _P, _I], _I),
     "nd_lowmodes_dynamic": ([_P, _I, _I, _D, _I, ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
+    "nd_lowmodes_ritz": ([_P, _I, _I, _D, _I, ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
     "nd_solve_Q2_eo": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_propagator": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), _D, _I, ctypes.POINTER(nd_prop_info)], _I),
     "nd_chebyshev_degree": ([_D, _D, ctypes.POINTER(_I)], _I),
@@ -185,6 +188,24 @@ def nd_unpack_spinor(ctx, canon, internal, prec, nrhs=1):
            "nd_unpack_spinor")
 
 
+def _f32(t):
+    """Canonical single-precision tensors may be complex64; the C-ABI sees interleaved float32."""
+    import torch
+    assert t.is_cuda and t.is_contiguous(), "canonical tensors must be contiguous CUDA tensors"
+    assert t.dtype in (torch.complex64, torch.float32)
+    return t
+
+
+def nd_pack_spinor_f32(ctx, internal, canon, prec, nrhs=1):
+    _check(ctx, lib().nd_pack_spinor_f32(ctx, _ptr(internal), _ptr(_f32(canon)), int(prec), int(nrhs)),
+           "nd_pack_spinor_f32")
+
+
+def nd_unpack_spinor_f32(ctx, canon, internal, prec, nrhs=1):
+    _check(ctx, lib().nd_unpack_spinor_f32(ctx, _ptr(_f32(canon)), _ptr(internal), int(prec), int(nrhs)),
+           "nd_unpack_spinor_f32")
+
+
 def nd_eo_tables(ctx, lex2eo, nbr):
     _check(ctx, lib().nd_eo_tables(ctx, _ptr(lex2eo), _ptr(nbr)), "nd_eo_tables")
 
@@ -233,17 +254,19 @@ def nd_solve(ctx, xs, b, shifts, tol, maxit=100000, inner=ND_FP64):
     return info
 
 
-def nd_lowmodes_dynamic(ctx, l_min, l_max, kappa_target=1e-6, maxit=1000000):
+def nd_lowmodes_dynamic(ctx, l_min, l_max, kappa_target=1e-6, maxit=1000000, method="filter"):
     """Low modes with l chosen in [l_min, l_max] by the largest relative gap, stopped at kappa_+- <=
-    kappa_target.  Returns (l, nu, rho, eval_Q2, info)."""
+    kappa_target; method "filter" (block Chebyshev-filtered subspace iteration) or "ritz" (the
+    paper's Ritz-functional minimiser).  Returns (l, nu, rho, eval_Q2, info)."""
+    fn = {"filter": lib().nd_lowmodes_dynamic, "ritz": lib().nd_lowmodes_ritz}[method]
     nu = (ctypes.c_double * l_max)()
     rho = (ctypes.c_double * l_max)()
     ev = (ctypes.c_double * (l_max + 1))()
     lo = ctypes.c_int()
     info = nd_lowmode_info()
-    st = lib().nd_lowmodes_dynamic(ctx, int(l_min), int(l_max), float(kappa_target), int(maxit), ctypes.byref(lo),
-                                   ctypes.cast(nu, _P), ctypes.cast(rho, _P), ctypes.cast(ev, _P), ctypes.byref(info))
-    _check(ctx, st, "nd_lowmodes_dynamic")
+    st = fn(ctx, int(l_min), int(l_max), float(kappa_target), int(maxit), ctypes.byref(lo), ctypes.cast(nu, _P),
+            ctypes.cast(rho, _P), ctypes.cast(ev, _P), ctypes.byref(info))
+    _check(ctx, st, "nd_lowmodes_" + ("dynamic" if method == "filter" else "ritz"))
     n = lo.value
     return n, list(nu)[:n], list(rho)[:n], list(ev)[:n + 1], info
 

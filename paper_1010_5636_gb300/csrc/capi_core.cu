@@ -215,6 +215,28 @@ nd_status nd_unpack_spinor(nd_ctx* c, double* canon, const void* internal, nd_pr
   return ND_OK;
 }
 
+nd_status nd_pack_spinor_f32(nd_ctx* c, void* internal, const float* canon, nd_prec prec, int nrhs) {
+  ND_TRY(check_ctx(c));
+  if (!internal || !canon || nrhs < 1 || prec < ND_FP64 || prec > ND_FP16)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_pack_spinor_f32: bad argument");
+  const size_t sb = nd_spinor_bytes(c, prec);
+  for (int k = 0; k < nrhs; ++k)
+    ND_TRY_CUDA(c, launch_pack_spinor_f32(c->g, (int)prec, static_cast<char*>(internal) + k * sb,
+                                          canon + k * c->V * 24, c->stream));
+  return ND_OK;
+}
+
+nd_status nd_unpack_spinor_f32(nd_ctx* c, float* canon, const void* internal, nd_prec prec, int nrhs) {
+  ND_TRY(check_ctx(c));
+  if (!internal || !canon || nrhs < 1 || prec < ND_FP64 || prec > ND_FP16)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_unpack_spinor_f32: bad argument");
+  const size_t sb = nd_spinor_bytes(c, prec);
+  for (int k = 0; k < nrhs; ++k)
+    ND_TRY_CUDA(c, launch_unpack_spinor_f32(c->g, (int)prec, canon + k * c->V * 24,
+                                            static_cast<const char*>(internal) + k * sb, c->stream));
+  return ND_OK;
+}
+
 nd_status nd_eo_tables(nd_ctx* c, int32_t* lex2eo, int32_t* nbr) {
   ND_TRY(check_ctx(c));
   if (!lex2eo || !nbr) return fail(c, ND_ERR_INVALID_ARG, "nd_eo_tables: null pointer");

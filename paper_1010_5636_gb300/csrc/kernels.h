@@ -109,6 +109,8 @@ cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st);
 // Pack / unpack between canonical FP64 ([lex][4][3][2]) and internal precision `prec`.
 cudaError_t launch_pack_spinor(const Geom& g, int prec, void* internal, const double* canon, cudaStream_t st);
 cudaError_t launch_unpack_spinor(const Geom& g, int prec, double* canon, const void* internal, cudaStream_t st);
+cudaError_t launch_pack_spinor_f32(const Geom& g, int prec, void* internal, const float* canon, cudaStream_t st);
+cudaError_t launch_unpack_spinor_f32(const Geom& g, int prec, float* canon, const void* internal, cudaStream_t st);
 // Compress canonical FP64 links ([4][lex][3][3][2]) into the internal (prec, recon) form.
 // For recon 8, *bad (device int) is set to 1 if any link is within the singular set.
 cudaError_t launch_pack_links(const Geom& g, int prec, int recon, void* internal, const double* canon, int* bad,

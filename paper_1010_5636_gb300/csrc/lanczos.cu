@@ -598,3 +598,204 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
   c->lam_max = lam_max;
   return ND_OK;
 }
+
+namespace {
+
+// Project v onto the complement of the k orthonormal FP64 fields at U (two passes).
+nd_status project_out(nd_ctx* c, const char* U, int k, size_t fs, void* v) {
+  for (int pass = 0; pass < 2 && k > 0; ++pass) {
+    std::vector<double> h;
+    ND_TRY(dots(c, U, fs, k, v, h));
+    for (auto& e : h) e = -e;
+    ND_TRY(lincomb(c, v, 1.0, v, U, fs, k, h));
+  }
+  return ND_OK;
+}
+
+// Complex (x, y) from the FP64 dot kernel.
+nd_status cdot(nd_ctx* c, const void* x, const void* y, double* re, double* im) {
+  double h[3];
+  ND_TRY_CUDA(c, blas_dot(c->g, 0, x, y, slot(c, c->red_scratch), c->stream));
+  ND_TRY(read_back(c, c->red_scratch, h, 3));
+  *re = h[0];
+  *im = h[1];
+  return ND_OK;
+}
+
+// v <- (cre + i cim) v  (complex scale, FP64 field)
+nd_status cscale(nd_ctx* c, void* v, double cre, double cim) {
+  std::vector<double> coef = {cre, cim};
+  return lincomb(c, v, 0.0, nullptr, static_cast<const char*>(v), 0, 1, coef);
+}
+
+}  // namespace
+
+// Minimise the Ritz functional mu(x) = (x, A x) / (x, x) of A = Q^2 / hi over x orthogonal to the k
+// orthonormal fields at U, starting from x (Sec. 2.3: the low modes are found by minimising the
+// Ritz functional of Q^2).  Nonlinear conjugate gradients in the form of Kalkreuter and Simma: the
+// search direction p is made orthogonal to x, and each step takes the exact minimum of mu on
+// span{x, p} (the lower eigenpair of the 2 x 2 projected matrix), so no line search is needed and
+// A x is carried along without an extra application.  Stops when ||A x - mu x|| <= tol.
+static nd_status ritz_cg(nd_ctx* c, const char* U, int k, size_t fs, void* x, double hi, double tol, int maxit,
+                         double* mu_out, double* gn_out, int* apps) {
+  void* y = field(c, "rf_y", 0);
+  void* g = field(c, "rf_g", 0);
+  void* p = field(c, "rf_p", 0);
+  void* q = field(c, "rf_q", 0);
+  void* z = field(c, "rf_z", 0);
+  if (!y || !g || !p || !q || !z) return fail(c, ND_ERR_OOM, "Ritz functional: workspace");
+  const double s = 1.0 / hi;
+  ND_TRY(project_out(c, U, k, fs, x));
+  double n2;
+  ND_TRY(norm2_64(c, x, &n2));
+  if (!(n2 > 0)) return fail(c, ND_ERR_BREAKDOWN, "Ritz functional: start vector lies in the found space");
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0 / std::sqrt(n2), x, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+  double mu = 0.0, gg = 0.0;
+  auto refresh = [&]() -> nd_status {
+    ND_TRY(apply_q2(c, y, x));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, y, s, y, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+    ++*apps;
+    double im;
+    ND_TRY(cdot(c, x, y, &mu, &im));
+    return ND_OK;
+  };
+  auto gradient = [&]() -> nd_status {
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, g, 1.0, y, -mu, x, false, slot(c, nullptr), c->stream));
+    ND_TRY(project_out(c, U, k, fs, g));
+    return norm2_64(c, g, &gg);
+  };
+  ND_TRY(refresh());
+  ND_TRY(gradient());
+  ND_TRY_CUDA(c, cudaMemcpyAsync(p, g, fs, cudaMemcpyDeviceToDevice, c->stream));
+  for (int it = 0; it < maxit && std::sqrt(gg) > tol; ++it) {
+    // q = p - (x, p) x on the complement of U, normalised
+    double are, aim;
+    ND_TRY(cdot(c, x, p, &are, &aim));
+    ND_TRY_CUDA(c, cudaMemcpyAsync(q, p, fs, cudaMemcpyDeviceToDevice, c->stream));
+    std::vector<double> coef = {-are, -aim};
+    ND_TRY(lincomb(c, q, 1.0, q, static_cast<const char*>(x), 0, 1, coef));
+    ND_TRY(project_out(c, U, k, fs, q));
+    double nq2;
+    ND_TRY(norm2_64(c, q, &nq2));
+    if (!(nq2 > 1e-300)) break;
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, q, 1.0 / std::sqrt(nq2), q, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+    ND_TRY(apply_q2(c, z, q));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, z, s, z, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+    ++*apps;
+    double bre, bim, d, dim;
+    ND_TRY(cdot(c, x, z, &bre, &bim));
+    ND_TRY(cdot(c, q, z, &d, &dim));
+    // lower eigenpair of [[mu, b], [conj(b), d]]: m and the vector (b, m - mu)
+    const double half = 0.5 * (mu - d), bb = bre * bre + bim * bim;
+    const double m = 0.5 * (mu + d) - std::sqrt(half * half + bb);
+    const double nv = std::sqrt(bb + (m - mu) * (m - mu));
+    if (!(nv > 0)) break;
+    const double cxr = bre / nv, cxi = bim / nv, cq = (m - mu) / nv;
+    // x <- cx x + cq q,  y <- cx y + cq z
+    ND_TRY(cscale(c, x, cxr, cxi));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0, x, cq, q, false, slot(c, nullptr), c->stream));
+    ND_TRY(cscale(c, y, cxr, cxi));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, y, 1.0, y, cq, z, false, slot(c, nullptr), c->stream));
+    mu = m;
+    if ((it + 1) % 25 == 0) {
+      // renormalise and recompute A x against drift
+      ND_TRY(norm2_64(c, x, &n2));
+      ND_TRY_CUDA(c, blas_axpby(c->g, 0, x, 1.0 / std::sqrt(n2), x, 0.0, nullptr, false, slot(c, nullptr), c->stream));
+      ND_TRY(refresh());
+    }
+    const double gg_old = gg;
+    ND_TRY(gradient());
+    // p <- g + beta (p - (x, p) x), Fletcher-Reeves beta
+    ND_TRY(cdot(c, x, p, &are, &aim));
+    coef = {-are, -aim};
+    ND_TRY(lincomb(c, p, 1.0, p, static_cast<const char*>(x), 0, 1, coef));
+    ND_TRY_CUDA(c, blas_axpby(c->g, 0, p, 1.0, g, gg / gg_old, p, false, slot(c, nullptr), c->stream));
+  }
+  *mu_out = mu * hi;
+  *gn_out = std::sqrt(gg) * hi;
+  return ND_OK;
+}
+
+// The paper's own low-mode method (Sec. 2.3): l_max + 1 vectors, each minimising the Ritz
+// functional of Q^2 on the complement of the ones before it (ritz_cg), then a Rayleigh-Ritz
+// step of Q^2 on all of them; l in [l_min, l_max] at the largest relative gap as in
+// nd_lowmodes_dynamic; if kappa_+- exceed the target, every vector is minimised again with a
+// ten times smaller gradient tolerance, until kappa_+- <= kappa_target.
+extern "C" nd_status nd_lowmodes_ritz(nd_ctx* c, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
+                                      double* nu_out, double* rho_out, double* evq2_out, nd_lowmode_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  if (l_min < 1 || l_max < l_min || l_max > 64 || !(kappa_target > 0) || maxit < 1)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_lowmodes_ritz: need 1 <= l_min <= l_max <= 64, kappa_target > 0");
+  if (!c->links[0]) return fail(c, ND_ERR_STATE, "nd_lowmodes_ritz: FP64 links not set");
+  auto t0 = std::chrono::steady_clock::now();
+  const size_t fs = (size_t)spinor_bytes(0, c->Vh);
+  double lam_max;
+  ND_TRY(lambda_max_estimate(c, 40, &lam_max));
+  const double hi = 1.01 * lam_max;
+  const int K = l_max + 1;
+  char* X = static_cast<char*>(field(c, "rf_X", 0, K));
+  char* AX = static_cast<char*>(field(c, "rf_AX", 0, K));
+  char* Y = static_cast<char*>(field(c, "rf_Y", 0, K));
+  char* Z = static_cast<char*>(field(c, "cf_Z", 0, l_max));
+  if (!X || !AX || !Y || !Z) return fail(c, ND_ERR_OOM, "nd_lowmodes_ritz: workspace");
+  for (int j = 0; j < K; ++j) ND_TRY_CUDA(c, blas_random(c->g, X + j * fs, 4242 + 7919ull * j, c->stream));
+  std::vector<double> theta, res, nu, rho;
+  int apps = 0, l = l_min;
+  double kp = INFINITY, km = INFINITY, tol = 1e-4;
+  const bool trace = std::getenv("ND_TRACE") != nullptr;
+  bool converged = false;
+  for (int round = 0; round < 12 && apps < maxit; ++round, tol *= 0.1) {
+    for (int j = 0; j < K && apps < maxit; ++j) {
+      double mu, gn;
+      ND_TRY(ritz_cg(c, X, j, fs, X + j * fs, hi, tol, maxit - apps, &mu, &gn, &apps));
+    }
+    ND_TRY(orthonormalise(c, X, K, fs));
+    ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, K, fs, theta, res));
+    apps += K;
+    double best = -1.0;
+    for (int j = l_min; j <= l_max; ++j) {
+      const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
+      const double gp = b > 0 ? (b - a) / b : 0.0;
+      if (gp > best) {
+        best = gp;
+        l = j;
+      }
+    }
+    ND_TRY_CUDA(c, cudaMemcpyAsync(Z, X, fs * l, cudaMemcpyDeviceToDevice, c->stream));
+    ND_TRY(ritz_of_Q(c, Z, l, nu, rho));
+    kappas(nu, rho, theta[l], &kp, &km);
+    if (trace)
+      std::fprintf(stderr, "nd_lowmodes_ritz: round %d tol %.1e apps %d l %d kappa+ %.3g kappa- %.3g\n", round, tol,
+                   apps, l, kp, km);
+    if (kp <= kappa_target && km <= kappa_target) {
+      converged = true;
+      break;
+    }
+  }
+  c->ws["rf_X"].first = X;
+  c->ws["rf_AX"].first = AX;
+  c->ws["rf_Y"].first = Y;
+  if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes_ritz: kappa target not reached");
+  c->lam_next = theta[l];
+  ND_TRY(store_modes(c, Z, l));
+  c->nu = nu;
+  c->rho = rho;
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (l_out) *l_out = l;
+  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
+  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
+  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
+  if (info) {
+    info->l = l;
+    info->iters = apps;
+    info->lambda_max = lam_max;
+    info->lambda_next = c->lam_next;
+    info->kappa_plus = kp;
+    info->kappa_minus = km;
+    info->max_rho = *std::max_element(rho.begin(), rho.end());
+    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  c->lam_max = lam_max;
+  return ND_OK;
+}

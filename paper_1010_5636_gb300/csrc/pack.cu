@@ -1,4 +1,4 @@
-// Layout conversion kernels: canonical FP64 (lex order, AoS) <-> internal even-odd SoA of
+// Layout conversion kernels: canonical FP64 or FP32 (lex order, AoS) <-> internal even-odd SoA of
 // each precision, link compression to 18 / 12 / 8 reals (Sec. 2.1), and the export of the
 // device's site tables for the bit-exact index test.
 #include "fields.cuh"
@@ -26,14 +26,14 @@ int64_t link_bytes(int prec, int recon, int64_t Vh) {
   return -1;
 }
 
-template <int P>
-__global__ void pack_spinor_kernel(const Geom g, void* internal, const double* canon) {
+template <int P, typename C>
+__global__ void pack_spinor_kernel(const Geom g, void* internal, const C* canon) {
   using T = typename Traits<P>::real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * g.Vh) return;
   const int p = i >= g.Vh ? 1 : 0, h = i - p * g.Vh;
   const Site s = site_of(g, p, h);
-  const double* src = canon + (int64_t)s.lex * 24;
+  const C* src = canon + (int64_t)s.lex * 24;
   Spinor<T> v;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -42,8 +42,8 @@ __global__ void pack_spinor_kernel(const Geom g, void* internal, const double* c
   SpinorIO<P>::store(v, internal, g.Vh, p, h);
 }
 
-template <int P>
-__global__ void unpack_spinor_kernel(const Geom g, double* canon, const void* internal) {
+template <int P, typename C>
+__global__ void unpack_spinor_kernel(const Geom g, C* canon, const void* internal) {
   using T = typename Traits<P>::real;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * g.Vh) return;
@@ -51,13 +51,13 @@ __global__ void unpack_spinor_kernel(const Geom g, double* canon, const void* in
   const Site s = site_of(g, p, h);
   Spinor<T> v;
   SpinorIO<P>::load(v, internal, g.Vh, p, h);
-  double* dst = canon + (int64_t)s.lex * 24;
+  C* dst = canon + (int64_t)s.lex * 24;
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      dst[2 * (3 * a + c)] = (double)v.s[a][c].re;
-      dst[2 * (3 * a + c) + 1] = (double)v.s[a][c].im;
+      dst[2 * (3 * a + c)] = (C)v.s[a][c].re;
+      dst[2 * (3 * a + c) + 1] = (C)v.s[a][c].im;
     }
 }
 
@@ -143,26 +143,41 @@ __global__ void pack_links_kernel(const Geom g, char* internal, const double* ca
 
 static int blocks_for(int64_t n) { return (int)((n + PACK_THREADS - 1) / PACK_THREADS); }
 
-cudaError_t launch_pack_spinor(const Geom& g, int prec, void* internal, const double* canon, cudaStream_t st) {
+template <typename C>
+static cudaError_t pack_t(const Geom& g, int prec, void* internal, const C* canon, cudaStream_t st) {
   const int b = blocks_for(2 * (int64_t)g.Vh);
   switch (prec) {
-    case P64: pack_spinor_kernel<P64><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
-    case P32: pack_spinor_kernel<P32><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
-    case P16: pack_spinor_kernel<P16><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
+    case P64: pack_spinor_kernel<P64, C><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
+    case P32: pack_spinor_kernel<P32, C><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
+    case P16: pack_spinor_kernel<P16, C><<<b, PACK_THREADS, 0, st>>>(g, internal, canon); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_unpack_spinor(const Geom& g, int prec, double* canon, const void* internal, cudaStream_t st) {
+template <typename C>
+static cudaError_t unpack_t(const Geom& g, int prec, C* canon, const void* internal, cudaStream_t st) {
   const int b = blocks_for(2 * (int64_t)g.Vh);
   switch (prec) {
-    case P64: unpack_spinor_kernel<P64><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
-    case P32: unpack_spinor_kernel<P32><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
-    case P16: unpack_spinor_kernel<P16><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
+    case P64: unpack_spinor_kernel<P64, C><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
+    case P32: unpack_spinor_kernel<P32, C><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
+    case P16: unpack_spinor_kernel<P16, C><<<b, PACK_THREADS, 0, st>>>(g, canon, internal); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_pack_spinor(const Geom& g, int prec, void* internal, const double* canon, cudaStream_t st) {
+  return pack_t(g, prec, internal, canon, st);
+}
+cudaError_t launch_unpack_spinor(const Geom& g, int prec, double* canon, const void* internal, cudaStream_t st) {
+  return unpack_t(g, prec, canon, internal, st);
+}
+cudaError_t launch_pack_spinor_f32(const Geom& g, int prec, void* internal, const float* canon, cudaStream_t st) {
+  return pack_t(g, prec, internal, canon, st);
+}
+cudaError_t launch_unpack_spinor_f32(const Geom& g, int prec, float* canon, const void* internal, cudaStream_t st) {
+  return unpack_t(g, prec, canon, internal, st);
 }
 
 cudaError_t launch_pack_links(const Geom& g, int prec, int recon, void* internal, const double* canon, int* bad,

@@ -1,9 +1,10 @@
 // Launch-shape autotuner for the repeatable Q launches (plain Q, one-parity blocks, several
 // right-hand sides).  Candidates: one warp per site in 64-thread (8 per SM) or 256-thread
-// blocks, and two or four warps per site (single RHS only).  Each candidate runs once untimed
-// and then five times on the caller's stream (the output is the same every time, and out never
-// aliases in for these launches); the fastest median wins.  The untimed launch keeps the first
-// candidate from paying for clock ramp-up and first touches of the data.  Choices live in memory for the process and, if
+// blocks, and two or four warps per site (single RHS only).  Each candidate runs twice untimed,
+// then three batches of eight back-to-back launches on the caller's stream (the output is the
+// same every time, and out never aliases in for these launches); the fastest median batch wins.
+// Batches measure the steady state the solvers see: one launch timed alone between host
+// synchronisations favoured shapes that are not faster in a stream of launches.  Choices live in memory for the process and, if
 // ND_AUTOTUNE_CACHE names a file, are read from and appended to it (one "key split threads"
 // line each).  ND_AUTOTUNE=0 turns tuning off (defaults: one warp per site, 64 threads).
 #include <algorithm>
@@ -87,9 +88,18 @@ cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st) {
     T.split = c.first;
     T.threads = c.second;
     std::vector<float> ts;
-    for (int rep = 0; rep < 6; ++rep) {
-      cudaEventRecord(e0, st);
+    for (int w = 0; w < 2; ++w) {
       cudaError_t e = launch_q(g, T, st);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return e;
+      }
+    }
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, st);
+      cudaError_t e = cudaSuccess;
+      for (int b = 0; b < 8 && e == cudaSuccess; ++b) e = launch_q(g, T, st);
       cudaEventRecord(e1, st);
       if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
         cudaEventDestroy(e0);
@@ -98,11 +108,11 @@ cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st) {
       }
       float ms = 0.f;
       cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) ts.push_back(ms);
+      ts.push_back(ms);
     }
     std::sort(ts.begin(), ts.end());
-    if (ts[2] < best) {
-      best = ts[2];
+    if (ts[1] < best) {
+      best = ts[1];
       pick = c;
     }
   }

@@ -1,4 +1,5 @@
-"""GPU parity of the dynamic choice of l with kappa-driven stopping (nd_lowmodes_dynamic, Sec. 2.3)
+"""GPU parity of the dynamic choice of l with kappa-driven stopping (nd_lowmodes_dynamic with the
+filtered subspace iteration, nd_lowmodes_ritz with the paper's Ritz-functional minimiser; Sec. 2.3)
 against the oracle's rule (oracle/lowmodes.choose_l) on the exact spectrum of the dense Q, and the
 paper's projector-deviation bound ||P_+- - (P_+-)_exact|| <= kappa (1 + 2 kappa) / (1 - 2 kappa (1 + 2 kappa))
 checked against the exact eigenvectors."""
@@ -30,8 +31,11 @@ def _projector_deviation(A, B):
     return float(np.sqrt(max(0.0, 1.0 - np.min(s) ** 2)))
 
 
-@pytest.mark.parametrize("l_min,l_max", [(4, 12), (2, 6), (9, 9)])
-def test_dynamic_l_vs_exact(nd, l_min, l_max):
+# the sequential Ritz-functional minimiser is far slower than the block filter: a shorter window and
+# a looser kappa target keep its case to seconds
+@pytest.mark.parametrize("l_min,l_max,method,kappa", [(4, 12, "filter", 1e-6), (2, 6, "filter", 1e-6),
+                                                      (9, 9, "filter", 1e-6), (2, 6, "ritz", 1e-4)])
+def test_dynamic_l_vs_exact(nd, l_min, l_max, method, kappa):
     import torch
     dims = (4, 4, 4, 4)
     U = synth.gauge_field(dims, "haar", seed=0)
@@ -43,13 +47,14 @@ def test_dynamic_l_vs_exact(nd, l_min, l_max):
     ctx = nd.nd_create(dims, m=M, s=S)
     try:
         nd.nd_set_links(ctx, dev(U), (18, 12, 12))
-        l, nu, rho, ev, info = nd.nd_lowmodes_dynamic(ctx, l_min, l_max, 1e-6, 200000)
-        print(f"l_min {l_min} l_max {l_max}: l {l} (oracle {l_exp}) kappa +{info.kappa_plus:.2e} -{info.kappa_minus:.2e}"
+        l, nu, rho, ev, info = nd.nd_lowmodes_dynamic(ctx, l_min, l_max, kappa, 200000, method)
+        print(f"{method} l_min {l_min} l_max {l_max}: l {l} (oracle {l_exp}) kappa +{info.kappa_plus:.2e} -{info.kappa_minus:.2e}"
               f" Q^2 applications {info.iters}")
         assert l == l_exp
-        assert info.kappa_plus <= 1e-6 and info.kappa_minus <= 1e-6
-        assert np.allclose(ev, ev_q2[: l + 1], rtol=1e-8)
-        assert np.allclose(np.sort(nu), np.sort(w[order[:l]]), rtol=1e-9, atol=1e-12)
+        assert info.kappa_plus <= kappa and info.kappa_minus <= kappa
+        # Ritz values are accurate to ~ (residual)^2: kappa 1e-6 gives 1e-8, 1e-4 still 1e-6
+        assert np.allclose(ev, ev_q2[: l + 1], rtol=1e-8 if kappa <= 1e-6 else 1e-6)
+        assert np.allclose(np.sort(nu), np.sort(w[order[:l]]), rtol=1e-9 if kappa <= 1e-6 else 1e-6, atol=1e-12)
         u_dev = torch.empty((l,) + (int(np.prod(dims)), 4, 3), dtype=torch.complex128, device="cuda")
         nd.nd_get_lowmodes(ctx, u_dev, l)
         u = host(u_dev).reshape(l, -1).T  # columns

@@ -138,6 +138,35 @@ def test_Q_parity_block(nd, parity, diag):
         nd.nd_destroy(ctx)
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_pack_round_trip_f32_canonical(nd, prec):
+    """Canonical complex64 fields: FP64 and FP32 internal storage carry them bit-exactly, FP16
+    to its storage precision; the FP32 form of a packed FP64 field is its rounding."""
+    import torch
+    dims = (4, 6, 2, 8)
+    psi = synth.spinor(dims, seed=1)
+    psi32 = psi.astype(np.complex64)
+    ctx = nd.nd_create(dims)
+    try:
+        f = torch.from_numpy(psi32).cuda()
+        buf = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
+        nd.nd_pack_spinor_f32(ctx, buf, f, prec)
+        back = torch.empty_like(f)
+        nd.nd_unpack_spinor_f32(ctx, back, buf, prec)
+        torch.cuda.synchronize()
+        if prec in (0, 1):
+            assert np.array_equal(host(back), psi32)
+        else:
+            assert rel(host(back), psi32) < 1e-3
+        if prec == 0:
+            nd.nd_pack_spinor(ctx, buf, dev(psi), 0)
+            nd.nd_unpack_spinor_f32(ctx, back, buf, 0)
+            torch.cuda.synchronize()
+            assert np.array_equal(host(back), psi32)
+    finally:
+        nd.nd_destroy(ctx)
+
+
 @pytest.mark.parametrize("dims", [(32, 16, 16, 16), (48, 24, 24, 24), (64, 32, 32, 32)])
 def test_Q_full_size_fp32(nd, dims):
     """The bench's lattices (near-identity links, as in the bandwidth sweep), whole-field parity."""
