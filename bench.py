@@ -9,10 +9,15 @@ value = algorithmic bytes of the step / step time, in GB/s; the per-site algorit
 are (24 input + 8 * 12 link + 24 output reals) * 4 bytes = 576 B (each input spinor and link
 counted once per pass, as the kernel's minimal DRAM traffic).
 
-Also measured and reported: the bandwidth sweep (FP64/FP32/FP16 x 18/12/8 links, full Q and
-half pass) and D_N applies per second on 16^3 x 32 Haar links with 20 Zolotarev poles and 20
-FP64 Lanczos modes, rational part solved to 1e-10: pure FP64 against mixed FP32 / FP16-storage
-inner iterations with FP64 defect correction.
+Also measured and reported: the end-to-end rate through the public API (complex64 host fields
+copied in and out every step, pipelined over two copy streams); the bandwidth sweep
+(FP64/FP32/FP16 x 18/12/8 links, full Q and half pass); D_N applies per second on 16^3 x 32 Haar
+links with 20 Zolotarev poles and 20 deflated low modes, rational part solved to 1e-10 (pure FP64
+against mixed FP32 / FP16-storage inner iterations with FP64 defect correction), the same with the
+paper's minmax polynomial (Clenshaw) and with l chosen dynamically under a kappa target, and a
+point-source propagator; the time per Clenshaw iteration per site on 24^3 x 48 (the paper's D_N
+timing unit); multi-RHS and multi-lattice Q launches; the force and the (Q^2)^{-1} solve on 16^4
+(whole lattice against the even-odd Schur complement).
 
 Replicas only on N GPUs: each rank runs the same independent workload (no collective on the
 data path); value sums the ranks' bytes over the slowest rank's time.
