@@ -703,6 +703,9 @@ def main():
         profile_case(nd, torch, args.case)
         return 0
     world, rank, local = dist_setup(args)
+    # a fixed launch shape (one warp per site, 64-thread blocks: the best of the shape sweeps) instead
+    # of the library's per-process autotuner, so that a run under a profiler launches the same kernels
+    os.environ.setdefault("ND_AUTOTUNE", "0")
     import torch
 
     import paper_1010_5636_gb300 as nd

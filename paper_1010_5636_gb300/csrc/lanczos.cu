@@ -343,16 +343,18 @@ nd_status rayleigh_ritz_q2(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size
 }  // namespace nd
 
 // One step of the filtered subspace iteration on the block X (k FP64 fields): filter every vector
-// with T_d(L(Q^2)) damping [lo, hi], lo = the largest Ritz value of the block, then re-orthonormalise
-// and Rayleigh-Ritz project.  FP32 filtering reaches residuals of about 1e-7 lambda_max; once the
+// but the `locked` lowest with T_d(L(Q^2)) damping [lo, hi], lo = the largest Ritz value of the
+// block, then re-orthonormalise and Rayleigh-Ritz project.  FP32 filtering reaches residuals of about 1e-7 lambda_max; once the
 // worst wanted residual is below 1e-6 lambda_max the filter runs in FP64.
 nd_status filter_step(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size_t fs, double hi, double worst,
-                      std::vector<double>& theta, std::vector<double>& res, int* apps) {
+                      std::vector<double>& theta, std::vector<double>& res, int* apps, int locked = 0) {
   const double lo = std::min(theta[k - 1], 0.5 * hi);
   const int prec = (c->links[1] && worst > 1e-6 * hi) ? 1 : 0;
   const int deg = prec == 1 ? 100 : 40;
-  for (int j = 0; j < k; ++j) ND_TRY(cheb_filter(c, prec, X + j * fs, deg, lo, hi));
-  *apps += k * deg;
+  // the lowest `locked` Ritz vectors have converged: they stay in the basis (orthogonalisation and
+  // Rayleigh-Ritz) but are not filtered again
+  for (int j = locked; j < k; ++j) ND_TRY(cheb_filter(c, prec, X + j * fs, deg, lo, hi));
+  *apps += (k - locked) * deg;
   ND_TRY(orthonormalise(c, X, k, fs));
   ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, k, fs, theta, res));
   *apps += k;
@@ -401,10 +403,13 @@ extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double
       break;
     }
     if (apps >= maxit) break;
+    // lock the leading wanted vectors that already meet a tenth of the target
+    int locked = 0;
+    while (locked < nwant && res[locked] <= 0.1 * tol * hi) ++locked;
     if (trace)
-      std::fprintf(stderr, "nd_lowmodes: it %d apps %d hi %.6g theta0 %.6g theta_l %.6g worst %.3g nconv %d\n", it,
-                   apps, hi, theta[0], theta[l], worst, nconv);
-    ND_TRY(filter_step(c, X, AX, Y, k, fs, hi, worst, theta, res, &apps));
+      std::fprintf(stderr, "nd_lowmodes: it %d apps %d hi %.6g theta0 %.6g theta_l %.6g worst %.3g nconv %d locked %d\n",
+                   it, apps, hi, theta[0], theta[l], worst, nconv, locked);
+    ND_TRY(filter_step(c, X, AX, Y, k, fs, hi, worst, theta, res, &apps, locked));
     lam_max = std::max(lam_max, theta[k - 1]);
   }
   // keep the workspace registry pointing at the right buffers after the swaps
@@ -526,6 +531,7 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
   const bool trace = std::getenv("ND_TRACE") != nullptr;
   bool converged = false;
   bool fixed = false;
+  double lock_frac = 0.1;
   int kb = k;  // current block size
   double best = -1.0;
   for (int it = 0; it < 1000; ++it) {
@@ -568,7 +574,21 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
       }
     }
     if (apps >= maxit) break;
-    ND_TRY(filter_step(c, X, AX, Y, kb, fs, hi, worst, theta, res, &apps));
+    // once l is fixed, lock the leading kept vectors whose residual already implies their share of
+    // the kappa target: rho_k ~ res_k / (2 sqrt(theta_k)) and d_k >= g = sqrt(theta_l) - sqrt(theta_{l-1}),
+    // so res_k <= 2 sqrt(theta_k) kappa g / sqrt(l) suffices; lock at lock_frac of that
+    int locked = 0;
+    if (fixed) {
+      const double g = std::sqrt(std::max(theta[l], 0.0)) - std::sqrt(std::max(theta[l - 1], 0.0));
+      while (locked < l &&
+             res[locked] <= lock_frac * 2.0 * std::sqrt(std::max(theta[locked], 0.0)) * kappa_target * g / std::sqrt((double)l))
+        ++locked;
+      if (locked == l && !(kp <= kappa_target && km <= kappa_target) && worst <= 1e-4 * hi) {
+        lock_frac *= 0.1;  // the estimate was too loose: tighten and filter everything again
+        locked = 0;
+      }
+    }
+    ND_TRY(filter_step(c, X, AX, Y, kb, fs, hi, worst, theta, res, &apps, locked));
     if (!fixed) lam_max = std::max(lam_max, theta[kb - 1]);
   }
   c->ws["cf_X"].first = X;
