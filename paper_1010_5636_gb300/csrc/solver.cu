@@ -384,8 +384,11 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   // floor_s: where the sloppy multi-shift recurrence stops being trusted; floor_in: the smallest
   // reduction asked of one FP32 correction solve.  ND_MIXED_FLOOR_S / ND_MIXED_FLOOR_IN in the
   // environment override them (tuning).
-  double floor_s = ps == 2 ? 1e-3 : 1e-6;
-  double floor_in = 1e-5;
+  // defaults from a grid on 16^3x32 Haar links with 20 deflated modes (D_N to 1e-10): FP32 sloppy
+  // floors 1e-5/1e-6/1e-7/3e-8 x correction floors 1e-4/1e-5/1e-6 gave 0.087-0.105 s per D_N, best
+  // at (1e-7, 1e-6); FP16 sloppy floors 1e-2/1e-3/1e-4 gave 0.113-0.129 s, best at (1e-4, 1e-6)
+  double floor_s = ps == 2 ? 1e-4 : 1e-7;
+  double floor_in = 1e-6;
   if (const char* e = std::getenv("ND_MIXED_FLOOR_S")) floor_s = std::atof(e);
   if (const char* e = std::getenv("ND_MIXED_FLOOR_IN")) floor_in = std::atof(e);
   void* bS = field(c, "mx_bS", ps);
