@@ -368,8 +368,8 @@ nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double si
   if (!t) return fail(c, ND_ERR_OOM, "residual: workspace");
   double* res = c->red_scratch + 8;
   ND_TRY(q_apply(c, 0, t, x));
-  ND_TRY(q_apply(c, 0, r, t, ascale, sigma, x));  // r = (ascale Q^2 + sigma) x
-  ND_TRY_CUDA(c, blas_axpby(c->g, 0, r, 1.0, b, -1.0, r, true, slot(c, res), c->stream));
+  // r = b - (ascale Q^2 + sigma) x in the second launch's epilogue, ||r||^2 reduced with it
+  ND_TRY(q_apply(c, 0, r, t, -ascale, -sigma, x, res, nullptr, b, 1.0));
   double h;
   ND_TRY(read_back(c, res, &h, 1));
   *rel = std::sqrt(h / bnorm2);
