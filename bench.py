@@ -463,10 +463,11 @@ def dn_phase(nd, torch, reps):
     res["propagator"] = {"s": round(t, 3), "cg_iters": pinf.iters, "passes": pinf.outer,
                          "sign_krylov_iters": pinf.sign_iters,
                          "resid": pinf.resid, "m_q": 0.1, "inner": "mixed_fp32, sign to 1e-12"}
-    # the paper's error control: l chosen in [8, 24] by the largest relative gap, modes refined until
-    # kappa_+- <= 1e-3; then the mixed FP32 D_N with those modes (eps from the chosen lambda_{l+1})
+    # the paper's error control: l chosen in [12, 24] by the largest relative gap, modes refined until
+    # kappa_+- <= 1e-2 (projector deviation <= ~1e-2); then the mixed FP32 D_N with those modes (eps from
+    # the chosen lambda_{l+1})
     t0 = time.perf_counter()
-    ld, _, _, _, lid = nd.nd_lowmodes_dynamic(ctx, 8, 24, 1e-3, 20000000)
+    ld, _, _, _, lid = nd.nd_lowmodes_dynamic(ctx, 12, 24, 1e-2, 20000000)
     t_dyn = time.perf_counter() - t0
     kmax = max(lid.kappa_plus, lid.kappa_minus)
     kk = kmax * (1 + 2 * kmax)
