@@ -421,6 +421,50 @@ class Lattice:
         nd_unpack_spinor(self.ctx, out, internal, prec, nrhs)
         return out
 
+    # canonical FP64 [V][4][3] complex128 tensors in and out
+
+    def Q(self, canon):
+        import torch
+        out = torch.empty_like(canon)
+        nd_apply_Q_canonical(self.ctx, out, canon)
+        return out
+
+    def sign(self, eta, **params):
+        """sign(Q) eta; params as dn_params (n_poles, eps, lambda_max, tol, maxit, inner_prec, ...)."""
+        import torch
+        out = torch.empty_like(eta)
+        info = nd_apply_sign(self.ctx, out, eta, dn_params(**params))
+        return out, info
+
+    def DN(self, eta, **params):
+        import torch
+        out = torch.empty_like(eta)
+        info = nd_apply_DN(self.ctx, out, eta, dn_params(**params))
+        return out, info
+
+    def propagator(self, b, tol=1e-10, maxit=10000, sign_tol=1e-12, **params):
+        """(D_N^m)^{-1} b to relative residual tol; sign(Q) to sign_tol, other params as dn_params."""
+        import torch
+        x = torch.empty_like(b)
+        info = nd_propagator(self.ctx, x, b, dn_params(tol=sign_tol, **params), tol, maxit)
+        return x, info
+
+    def lowmodes(self, l=None, tol=1e-12, maxit=100000, l_range=None, kappa=1e-6, method="filter"):
+        """Fixed l (nd_lowmodes), or l chosen in l_range = (l_min, l_max) under a kappa target."""
+        if l_range is None:
+            return nd_lowmodes(self.ctx, l, tol, maxit)
+        return nd_lowmodes_dynamic(self.ctx, l_range[0], l_range[1], kappa, maxit, method)
+
+    def solve_Q2(self, b, tol=1e-10, maxit=100000, inner=ND_FP64, even_odd=False):
+        """x = (Q^2)^{-1} b, whole lattice (nd_solve) or through the Schur complement."""
+        import torch
+        x = torch.empty_like(b)
+        if even_odd:
+            info = nd_solve_Q2_eo(self.ctx, x, b, tol, maxit, inner)
+        else:
+            info = nd_solve(self.ctx, [x], b, [0.0], tol, maxit, inner)
+        return x, info
+
     def close(self):
         if getattr(self, "ctx", None):
             nd_destroy(self.ctx)
