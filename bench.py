@@ -193,7 +193,7 @@ def oracle_baseline(seconds_target=15.0):
         wilson.apply_Q(U, psi, DIMS, -1.4)
         n += 1
         el = time.perf_counter() - t0
-        if el >= seconds_target or n >= 50:
+        if el >= seconds_target or n >= 400:
             break
     rate = n * V / el
     return {"value": rate * site_bytes(1, RECON) / 1e9, "unit": "GB/s", "cores": wilson.get_threads(),
