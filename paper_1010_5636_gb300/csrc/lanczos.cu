@@ -361,6 +361,54 @@ nd_status filter_step(nd_ctx* c, char*& X, char*& AX, char*& Y, int k, size_t fs
   return ND_OK;
 }
 
+// The l in [l_min, l_max] with the largest relative gap (sqrt(theta_l) - sqrt(theta_{l-1})) / sqrt(theta_l)
+// between the last kept (theta_{l-1}) and the first remaining (theta_l) Ritz value of Q^2, the
+// smallest l on ties; *gap receives that gap.
+static int choose_l_by_gap(const std::vector<double>& theta, int l_min, int l_max, double* gap) {
+  int l = l_min;
+  double best = -1.0;
+  for (int j = l_min; j <= l_max; ++j) {
+    const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
+    const double g = b > 0 ? (b - a) / b : 0.0;
+    if (g > best) {
+      best = g;
+      l = j;
+    }
+  }
+  *gap = best;
+  return l;
+}
+
+// Keep l modes (FP64 fields at U) in the context and fill the caller's outputs.
+static nd_status finish_lowmodes(nd_ctx* c, const void* U, int l, const std::vector<double>& nu,
+                                 const std::vector<double>& rho, const std::vector<double>& theta, double lam_max,
+                                 int apps, std::chrono::steady_clock::time_point t0, int* l_out, double* nu_out,
+                                 double* rho_out, double* evq2_out, nd_lowmode_info* info) {
+  c->lam_next = theta[l];
+  ND_TRY(store_modes(c, U, l));
+  c->nu = nu;
+  c->rho = rho;
+  double kp, km;
+  kappas(nu, rho, c->lam_next, &kp, &km);
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (l_out) *l_out = l;
+  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
+  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
+  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
+  if (info) {
+    info->l = l;
+    info->iters = apps;
+    info->lambda_max = lam_max;
+    info->lambda_next = c->lam_next;
+    info->kappa_plus = kp;
+    info->kappa_minus = km;
+    info->max_rho = *std::max_element(rho.begin(), rho.end());
+    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  c->lam_max = lam_max;
+  return ND_OK;
+}
+
 // Low modes by Chebyshev-filtered subspace iteration on Q^2: a block of k = l+1+buffer FP64
 // vectors is filtered with T_d(L(Q^2)) (damping [lo, lambda_max], lo = the largest Ritz value
 // of the block), re-orthonormalised in FP64 and Rayleigh-Ritz projected with FP64 Q^2.  The
@@ -417,30 +465,9 @@ extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double
   c->ws["cf_AX"].first = AX;
   c->ws["cf_Y"].first = Y;
   if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes: filtered subspace iteration did not converge");
-  c->lam_next = theta[l];
   std::vector<double> nu, rho;
   ND_TRY(ritz_of_Q(c, X, l, nu, rho));
-  ND_TRY(store_modes(c, X, l));
-  c->nu = nu;
-  c->rho = rho;
-  double kp, km;
-  kappas(nu, rho, c->lam_next, &kp, &km);
-  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
-  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
-  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
-  if (info) {
-    info->l = l;
-    info->iters = apps;
-    info->lambda_max = lam_max;
-    info->lambda_next = c->lam_next;
-    info->kappa_plus = kp;
-    info->kappa_minus = km;
-    info->max_rho = *std::max_element(rho.begin(), rho.end());
-    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  }
-  c->lam_max = lam_max;
-  return ND_OK;
+  return finish_lowmodes(c, X, l, nu, rho, theta, lam_max, apps, t0, nullptr, nu_out, rho_out, evq2_out, info);
 }
 
 extern "C" nd_status nd_set_lowmodes(nd_ctx* c, int l, const double* evecs, const double* nu, double lambda_next,
@@ -536,16 +563,7 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
   double best = -1.0;
   for (int it = 0; it < 1000; ++it) {
     if (!fixed) {
-      // the candidate with the largest relative gap
-      best = -1.0;
-      for (int j = l_min; j <= l_max; ++j) {
-        const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
-        const double g = b > 0 ? (b - a) / b : 0.0;
-        if (g > best) {
-          best = g;
-          l = j;
-        }
-      }
+      l = choose_l_by_gap(theta, l_min, l_max, &best);
       // once every candidate's Ritz value is settled (residual <= 1e-3 lambda_max bounds its error
       // by ~1e-6 lambda_max^2 / gap), l is fixed and the block shrinks to the lowest
       // max(l + 9, 2 (l + 1)) Ritz vectors: the rest of the work only refines the kept modes
@@ -596,27 +614,7 @@ extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double
   c->ws["cf_Y"].first = Y;
   if (!converged)
     return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes_dynamic: kappa target not reached within maxit Q^2 applications");
-  c->lam_next = theta[l];
-  ND_TRY(store_modes(c, Z, l));
-  c->nu = nu;
-  c->rho = rho;
-  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (l_out) *l_out = l;
-  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
-  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
-  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
-  if (info) {
-    info->l = l;
-    info->iters = apps;
-    info->lambda_max = lam_max;
-    info->lambda_next = c->lam_next;
-    info->kappa_plus = kp;
-    info->kappa_minus = km;
-    info->max_rho = *std::max_element(rho.begin(), rho.end());
-    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  }
-  c->lam_max = lam_max;
-  return ND_OK;
+  return finish_lowmodes(c, Z, l, nu, rho, theta, lam_max, apps, t0, l_out, nu_out, rho_out, evq2_out, info);
 }
 
 namespace {
@@ -773,15 +771,8 @@ extern "C" nd_status nd_lowmodes_ritz(nd_ctx* c, int l_min, int l_max, double ka
     ND_TRY(orthonormalise(c, X, K, fs));
     ND_TRY(rayleigh_ritz_q2(c, X, AX, Y, K, fs, theta, res));
     apps += K;
-    double best = -1.0;
-    for (int j = l_min; j <= l_max; ++j) {
-      const double a = std::sqrt(std::max(theta[j - 1], 0.0)), b = std::sqrt(std::max(theta[j], 0.0));
-      const double gp = b > 0 ? (b - a) / b : 0.0;
-      if (gp > best) {
-        best = gp;
-        l = j;
-      }
-    }
+    double best;
+    l = choose_l_by_gap(theta, l_min, l_max, &best);
     ND_TRY_CUDA(c, cudaMemcpyAsync(Z, X, fs * l, cudaMemcpyDeviceToDevice, c->stream));
     ND_TRY(ritz_of_Q(c, Z, l, nu, rho));
     kappas(nu, rho, theta[l], &kp, &km);
@@ -797,25 +788,5 @@ extern "C" nd_status nd_lowmodes_ritz(nd_ctx* c, int l_min, int l_max, double ka
   c->ws["rf_AX"].first = AX;
   c->ws["rf_Y"].first = Y;
   if (!converged) return fail(c, ND_ERR_NOT_CONVERGED, "nd_lowmodes_ritz: kappa target not reached");
-  c->lam_next = theta[l];
-  ND_TRY(store_modes(c, Z, l));
-  c->nu = nu;
-  c->rho = rho;
-  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
-  if (l_out) *l_out = l;
-  if (nu_out) std::copy(nu.begin(), nu.end(), nu_out);
-  if (rho_out) std::copy(rho.begin(), rho.end(), rho_out);
-  if (evq2_out) std::copy(theta.begin(), theta.begin() + l + 1, evq2_out);
-  if (info) {
-    info->l = l;
-    info->iters = apps;
-    info->lambda_max = lam_max;
-    info->lambda_next = c->lam_next;
-    info->kappa_plus = kp;
-    info->kappa_minus = km;
-    info->max_rho = *std::max_element(rho.begin(), rho.end());
-    info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-  }
-  c->lam_max = lam_max;
-  return ND_OK;
+  return finish_lowmodes(c, Z, l, nu, rho, theta, lam_max, apps, t0, l_out, nu_out, rho_out, evq2_out, info);
 }
