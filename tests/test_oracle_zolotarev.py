@@ -45,3 +45,16 @@ def test_shifts_positive_and_delta_decreasing():
         assert np.all(np.diff(c["sigma"]) > 0)
         assert c["delta"] < prev
         prev = c["delta"]
+
+
+@pytest.mark.parametrize("eps", [0.5, 0.1, 1e-2, 1e-4])
+def test_one_pole_closed_form(eps):
+    """n = 1: R(x) = b x / (x^2 + sigma) on [k, 1], k = sqrt(eps).  Equioscillation at x = k, the
+    maximum x = sqrt(sigma) and x = 1 gives R(k) = R(1), hence sigma = k, and
+    1 - R(1) = R(sqrt(k)) - 1 fixes b = 2 / (1/(1 + k) + 1/(2 k^(1/2))), delta = 1 - b/(1 + k)."""
+    z = zolotarev.zolotarev(1, eps)
+    k = np.sqrt(eps)
+    b = 2.0 / (1.0 / (1.0 + k) + 1.0 / (2.0 * eps ** 0.25))
+    assert float(z["sigma"][0]) == pytest.approx(k, rel=1e-14)
+    assert float(z["b"][0]) == pytest.approx(b, rel=1e-14)
+    assert float(z["delta"]) == pytest.approx(1.0 - b / (1.0 + k), rel=1e-12)

@@ -23,3 +23,15 @@ def test_bad_arguments():
         nd.nd_zolotarev(0, 1e-3)
     with pytest.raises(nd.NdError):
         nd.nd_zolotarev(8, 1.5)
+
+
+@pytest.mark.parametrize("eps", [0.5, 1e-2, 1e-4])
+def test_one_pole_closed_form(eps):
+    """The host generator at n = 1 against sigma = sqrt(eps), b = 2 / (1/(1 + k) + 1/(2 k^(1/2)))."""
+    import paper_1010_5636_gb300 as nd
+    sig, b, delta = nd.nd_zolotarev(1, eps)
+    k = np.sqrt(eps)
+    bb = 2.0 / (1.0 / (1.0 + k) + 1.0 / (2.0 * eps ** 0.25))
+    assert sig[0] == pytest.approx(k, rel=1e-13)
+    assert b[0] == pytest.approx(bb, rel=1e-13)
+    assert delta == pytest.approx(1.0 - bb / (1.0 + k), rel=1e-9)
