@@ -230,6 +230,12 @@ nd_status nd_set_lowmodes(nd_ctx* ctx, int l, const double* evecs_dev, const dou
 /* Copy the context's low modes out: evecs_dev [l][V*12] complex canonical (device), nu[l] (host). */
 nd_status nd_get_lowmodes(nd_ctx* ctx, double* evecs_dev, double* nu);
 
+/* The context's low-mode state (host outputs, each may be NULL): the number of modes kept, the
+ * estimate of lambda_{l+1}(Q^2) sign(Q) takes eps from, and the lambda_max(Q^2) estimate (0 if
+ * none yet).  With nd_get_lowmodes it is what a caller saves to restore the modes later through
+ * nd_set_lowmodes (a checkpoint of the expensive part of D_N). */
+nd_status nd_lowmode_state(nd_ctx* ctx, int* l, double* lambda_next, double* lambda_max);
+
 /* Estimate lambda_max(Q^2) with iters Lanczos steps (upper Ritz value; not padded). */
 nd_status nd_lambda_max(nd_ctx* ctx, int iters, double* lambda_max);
 

@@ -87,6 +87,7 @@ _SIGS = {
     "nd_apply_Qhat": ([_P, _P, _P, _I], _I),
     "nd_lowmodes_dynamic": ([_P, _I, _I, _D, _I, ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
     "nd_lowmodes_ritz": ([_P, _I, _I, _D, _I, ctypes.POINTER(_I), _P, _P, _P, ctypes.POINTER(nd_lowmode_info)], _I),
+    "nd_lowmode_state": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_D), ctypes.POINTER(_D)], _I),
     "nd_solve_Q2_eo": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_propagator": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), _D, _I, ctypes.POINTER(nd_prop_info)], _I),
     "nd_chebyshev_degree": ([_D, _D, ctypes.POINTER(_I)], _I),
@@ -295,6 +296,34 @@ def nd_get_lowmodes(ctx, evecs, l):
     nu = (ctypes.c_double * l)()
     _check(ctx, lib().nd_get_lowmodes(ctx, _ptr(_f64(evecs)), ctypes.cast(nu, _P)), "nd_get_lowmodes")
     return list(nu)
+
+
+def nd_lowmode_state(ctx):
+    """(l, lambda_next, lambda_max) of the context's low modes."""
+    l, ln, lm = ctypes.c_int(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().nd_lowmode_state(ctx, ctypes.byref(l), ctypes.byref(ln), ctypes.byref(lm)), "nd_lowmode_state")
+    return l.value, ln.value, lm.value
+
+
+def save_lowmodes(ctx, path):
+    """Checkpoint the context's low modes (vectors, nu, lambda_next) to a .npz file."""
+    import numpy as np
+    import torch
+    l, lam_next, lam_max = nd_lowmode_state(ctx)
+    V = nd_volume(ctx)
+    ev = torch.empty((max(l, 1), V, 4, 3), dtype=torch.complex128, device="cuda")
+    nu = nd_get_lowmodes(ctx, ev, l) if l else []
+    np.savez(path, evecs=ev[:l].cpu().numpy(), nu=np.asarray(nu, dtype=np.float64), lambda_next=lam_next,
+             lambda_max=lam_max)
+
+
+def load_lowmodes(ctx, path):
+    """Restore low modes saved by save_lowmodes (rho and kappa are recomputed on the GPU)."""
+    import numpy as np
+    import torch
+    d = np.load(path)
+    return nd_set_lowmodes(ctx, torch.from_numpy(np.ascontiguousarray(d["evecs"])).cuda(), list(d["nu"]),
+                           float(d["lambda_next"]))
 
 
 def nd_lambda_max(ctx, iters=50):

@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/nd.h"
 #include "kernels.h"
 
@@ -54,6 +56,16 @@ struct nd_ctx {
 };
 
 namespace nd {
+
+// A named range on the NVTX timeline around a solver phase: visible to profilers (ncu --nvtx),
+// a no-op when none is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 
 nd_status fail(nd_ctx* c, nd_status st, const std::string& msg);
 nd_status fail_cuda(nd_ctx* c, cudaError_t e, const char* what);

@@ -254,6 +254,7 @@ static nd_status solve_action(nd_ctx* c, const double* phi, double tol, int maxi
 
 extern "C" nd_status nd_force(nd_ctx* c, double* F, const double* phi, double tol, int maxit, nd_prec inner,
                               nd_solve_info* info) {
+  NvtxRange range("nd.force");
   if (c && !F) return fail(c, ND_ERR_INVALID_ARG, "nd_force: null output");
   void *X, *Y;
   ND_TRY(solve_action(c, phi, tol, maxit, inner, &X, &Y, nullptr, info));
@@ -266,6 +267,7 @@ extern "C" nd_status nd_force(nd_ctx* c, double* F, const double* phi, double to
 
 extern "C" nd_status nd_link_gradient(nd_ctx* c, double* G, double* Xout, double* S, const double* phi, double tol,
                                       int maxit, nd_prec inner, nd_solve_info* info) {
+  NvtxRange range("nd.link_gradient");
   if (c && !G) return fail(c, ND_ERR_INVALID_ARG, "nd_link_gradient: null output");
   void *X, *Y;
   ND_TRY(solve_action(c, phi, tol, maxit, inner, &X, &Y, S, info));

@@ -415,6 +415,7 @@ static nd_status finish_lowmodes(nd_ctx* c, const void* U, int l, const std::vec
 // filter runs in FP32 while the residuals are above 1e-5 lambda_max, then in FP64.
 extern "C" nd_status nd_lowmodes(nd_ctx* c, int l, double tol, int maxit, double* nu_out, double* rho_out,
                                  double* evq2_out, nd_lowmode_info* info) {
+  NvtxRange range("nd.lowmodes");
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   if (l < 1 || l > 64 || !(tol > 0) || maxit < 1) return fail(c, ND_ERR_INVALID_ARG, "nd_lowmodes: 1 <= l <= 64");
@@ -521,6 +522,14 @@ extern "C" nd_status nd_get_lowmodes(nd_ctx* c, double* evecs, double* nu) {
   return ND_OK;
 }
 
+extern "C" nd_status nd_lowmode_state(nd_ctx* c, int* l, double* lambda_next, double* lambda_max) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (l) *l = c->nlow;
+  if (lambda_next) *lambda_next = c->lam_next;
+  if (lambda_max) *lambda_max = c->lam_max;
+  return ND_OK;
+}
+
 // Low modes with the number l chosen dynamically and kappa_+- driving the stopping (Sec. 2.3).
 // The block iteration above runs for l_max + 1 wanted modes.  After each step the candidate l in
 // [l_min, l_max] with the largest relative gap (sqrt(theta_{l+1}) - sqrt(theta_l)) / sqrt(theta_{l+1})
@@ -532,6 +541,7 @@ extern "C" nd_status nd_get_lowmodes(nd_ctx* c, double* evecs, double* nu) {
 // fixed and the block shrinks to the vectors needed for the kept modes.
 extern "C" nd_status nd_lowmodes_dynamic(nd_ctx* c, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
                                          double* nu_out, double* rho_out, double* evq2_out, nd_lowmode_info* info) {
+  NvtxRange range("nd.lowmodes_dynamic");
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   if (l_min < 1 || l_max < l_min || l_max > 64 || !(kappa_target > 0) || maxit < 1)
@@ -741,6 +751,7 @@ static nd_status ritz_cg(nd_ctx* c, const char* U, int k, size_t fs, void* x, do
 // ten times smaller gradient tolerance, until kappa_+- <= kappa_target.
 extern "C" nd_status nd_lowmodes_ritz(nd_ctx* c, int l_min, int l_max, double kappa_target, int maxit, int* l_out,
                                       double* nu_out, double* rho_out, double* evq2_out, nd_lowmode_info* info) {
+  NvtxRange range("nd.lowmodes_ritz");
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   if (l_min < 1 || l_max < l_min || l_max > 64 || !(kappa_target > 0) || maxit < 1)

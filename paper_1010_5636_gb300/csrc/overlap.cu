@@ -29,6 +29,7 @@ using namespace nd;
 // written over b_{k+2} (two b buffers rotate).
 static nd_status clenshaw(nd_ctx* c, int ps, const void* src64, void* y64, const std::vector<double>& co, double lam,
                           double eps) {
+  NvtxRange range("nd.clenshaw");
   const int n = (int)co.size() - 1;
   const double alpha = 4.0 / (lam * (1.0 - eps)), beta = -2.0 * (1.0 + eps) / (1.0 - eps);
   if (n == 0) {
@@ -69,6 +70,7 @@ static nd_status clenshaw(nd_ctx* c, int ps, const void* src64, void* y64, const
 // in: canonical FP64 (packed here), or the internal FP64 layout when `internal`.
 static nd_status sign_impl(nd_ctx* c, const double* in, const nd_dn_params* p, nd_dn_info* info, void** sign64,
                            void** eta64, bool internal = false) {
+  NvtxRange range("nd.sign");
   if (!c || !p) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   const bool poly = p->approx == ND_SIGN_CHEBYSHEV;

@@ -48,6 +48,7 @@ double dot_re(nd_ctx* c, const void* x, const void* y, nd_status* st) {
 
 extern "C" nd_status nd_propagator(nd_ctx* c, double* x_out, const double* b_in, const nd_dn_params* p, double tol,
                                    int maxit, nd_prop_info* info) {
+  NvtxRange range("nd.propagator");
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   if (!p || !x_out || !b_in || x_out == b_in || !(tol > 0) || maxit < 1)

@@ -146,6 +146,7 @@ extern "C" nd_status nd_apply_Qhat(nd_ctx* c, void* out, const void* in, nd_prec
 
 extern "C" nd_status nd_solve_Q2_eo(nd_ctx* c, double* x_out, const double* b_in, double tol, int maxit, nd_prec inner,
                                     nd_solve_info* info) {
+  NvtxRange range("nd.solve_q2_eo");
   if (!c) return ND_ERR_INVALID_ARG;
   if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
   if (!x_out || !b_in || x_out == b_in || !(tol > 0) || maxit < 1 || inner < ND_FP64 || inner > ND_FP16)

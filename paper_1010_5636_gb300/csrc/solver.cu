@@ -148,6 +148,7 @@ static nd_ms_graph* ms_graph(nd_ctx* c, int ps, int px, bool ymode, void* r, voi
 nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x_or_y, const std::vector<double>& sigma,
                    const std::vector<double>& tol, const std::vector<double>& w, double ascale, int maxit,
                    MsResult* out) {
+  NvtxRange range("nd.multishift_cg");
   const int n = (int)sigma.size();
   if (n < 1 || n > CG_NMAX) return fail(c, ND_ERR_INVALID_ARG, "multi-shift CG: 1..32 shifts");
   const size_t fs = (size_t)spinor_bytes(ps, c->Vh);
@@ -249,6 +250,7 @@ static cudaError_t bcg_iteration(nd_ctx* c, cudaStream_t st, int ps, char* r, ch
 // multi-RHS Q launch per step for all of them).  b, x: nsys consecutive fields of precision ps.
 nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<double>& sigma,
                   const std::vector<double>& tol, double ascale, int maxit, std::vector<int>* iters) {
+  NvtxRange range("nd.batched_cg");
   const int nsys = (int)sigma.size();
   if (nsys < 1 || nsys > 1024) return fail(c, ND_ERR_INVALID_ARG, "batched CG: 1..1024 systems");
   if (!c->links[ps]) return fail(c, ND_ERR_STATE, "batched CG: links not set in the Krylov precision");
@@ -379,6 +381,7 @@ nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double si
 nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, const std::vector<double>& sigma,
                            const std::vector<double>& tol, double ascale, int maxit, MixedStats* st,
                            nd_status (*sink)(void*, int, void*), void* sink_ctx) {
+  NvtxRange range("nd.mixed_solve");
   const int n = (int)sigma.size();
   // Sloppy pass: the Krylov vectors in ps, the shifted solutions in FP32.
   // floor_s: where the sloppy multi-shift recurrence stops being trusted; floor_in: the smallest
