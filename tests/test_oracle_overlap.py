@@ -176,3 +176,27 @@ def test_propagator_vs_dense(lat2, m_q):
     delta = overlap.zolo(16, eps)["delta"]
     bound = (info["resid"] * np.linalg.norm(b) + (1 + S) * (delta + 1e-12) * np.linalg.norm(x)) / m_q
     assert np.linalg.norm(x.reshape(-1) - x_ex) <= bound
+
+
+def test_massive_dn_spectrum_on_circle(lat2):
+    """With sign(Q)^2 = 1, D_N = (1 + gamma5 sign Q)/abar has its spectrum on the circle |z - 1/abar| =
+    1/abar, so D_N^m = (1 - abar m/2) D_N + m has it on |z - c| = r with r = (1 - abar m/2)/abar and
+    c = r + m.  The oracle's D_N^m, assembled column by column on 2^4, must put every eigenvalue
+    there to within the approximation's error."""
+    dims, U, lm, S_ex, lam_max, eps = lat2
+    m_q = 0.3
+    n = int(np.prod(dims)) * 12
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, dtype=np.complex128)
+        e[j] = 1.0
+        d, info = overlap.dn_apply(U, dims, M, S, e.reshape(-1, 4, 3), lam_max, eps, 16, 1e-13, lm["u"], lm["nu"],
+                                   m_q=m_q)
+        cols.append(d.reshape(-1))
+    D = np.array(cols).T
+    abar = 1.0 / (1.0 + S)
+    r = (1.0 - abar * m_q / 2.0) / abar
+    ev = np.linalg.eigvals(D)
+    assert np.max(np.abs(np.abs(ev - (r + m_q)) - r)) <= 1e-9
+    # the massless limit sits on the circle through 0, and the mass shifts its centre
+    assert np.min(ev.real) >= m_q - 1e-9
