@@ -6,7 +6,7 @@ import pytest
 from oracle import chebyshev
 
 
-@pytest.mark.parametrize("n,eps", [(0, 0.3), (1, 0.1), (8, 0.05), (40, 1e-2), (150, 2e-3)])
+@pytest.mark.parametrize("n,eps", [(0, 0.3), (1, 0.1), (8, 0.05), (40, 1e-2), (150, 2e-3), (300, 1e-3)])
 def test_table_matches_oracle(n, eps):
     import paper_1010_5636_gb300 as nd
     c, delta = nd.nd_chebyshev(n, eps)
