@@ -124,7 +124,10 @@ nd_status nd_apply_Q_parity(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_p
  * lattice of ctxs[k] (every context must hold links in prec with the same link form).  Tiles of
  * 64 sites x one RHS are walked lattice by lattice with the RHS fastest, so each lattice's links
  * are read from DRAM once for all its RHS.  Runs on `stream` (a cudaStream_t).  Errors are
- * reported on ctxs[0]. */
+ * reported on ctxs[0].  The work list is staged in a device buffer owned by ctxs[0] and filled by a
+ * copy from pageable host memory on `stream`: calls that share ctxs[0] must use one stream (a call on
+ * another stream could overwrite the list while an earlier launch still reads it), and the call
+ * cannot be captured into a CUDA graph. */
 nd_status nd_apply_Q_batched(nd_ctx* const* ctxs, int nlat, void* const* out_dev, const void* const* in_dev,
                              const int* nrhs, nd_prec prec, void* stream);
 
@@ -138,7 +141,10 @@ nd_status nd_apply_Q_canonical(nd_ctx* ctx, double* out_dev, const double* in_de
  * It allocates nothing: the reduction scratch is a static device array of 256 KiB per GPU
  * (kept until exit), which limits the lattice to 4194304 sites (larger: ND_ERR_INVALID_ARG).
  * The first call on a device looks up that array's device address; make it before any
- * stream capture.  All calls share the array: calls that overlap on the GPU race on it.
+ * stream capture.  That address is kept for the life of the process: after cudaDeviceReset (which
+ * also invalidates every nd_ctx of that device) this entry point must not be called again.
+ * All calls share the array: calls that overlap on the GPU race on it, and the earlier of two
+ * overlapping calls can return the other call's (stale) norms without reporting an error.
  * Synchronises the context's stream. */
 nd_status nd_apply_Q_norms_static(nd_ctx* ctx, void* out_dev, const void* in_dev, nd_prec prec, double* norms);
 
@@ -153,7 +159,9 @@ typedef struct {
 } nd_solve_info;
 
 /* Solve (Q^2 + shifts[k]) x_k = b for k < n (multi-shift CG, one Krylov space; each shift
- * stops at relative residual tol).  b_dev and x_dev[k] are canonical FP64 device spinors;
+ * stops at relative residual tol).  These are the shifted inverses that the rational approximation
+ * of sign(Q) is built from (Sec. 2.2, the approximation of sign(Q); Q as in Sec. 2.1); the paper
+ * itself evaluates a polynomial instead and prints no solver.  b_dev and x_dev[k] are canonical FP64 device spinors;
  * x_dev is a host array of n device pointers.  inner = ND_FP64 runs everything in FP64;
  * ND_FP32 / ND_FP16 run the Krylov iterations in that storage precision with FP64
  * reductions and refine every shift in FP64 (defect correction) down to tol.
@@ -193,8 +201,9 @@ typedef struct {
   double time_ms;
 } nd_lowmode_info;
 
-/* Compute the l lowest modes of Q^2 in FP64 (thick-restart Lanczos), then the Rayleigh-Ritz
- * eigenpairs (nu_k, u_k) of Q on their span, the residues rho_k and kappa_+- (Sec. 2.3).
+/* Compute the l lowest modes of Q^2 (Chebyshev-filtered block subspace iteration: filter in FP32
+ * until the residuals are small, then FP64; FP64 orthogonalisation and Rayleigh-Ritz of Q^2), then the
+ * Rayleigh-Ritz eigenpairs (nu_k, u_k) of Q on their span, the residues rho_k and kappa_+- (Sec. 2.3).
  * The basis stays in the context for nd_apply_DN.  Host outputs (may be NULL):
  * nu[l], rho[l], eval_Q2[l+1] (the Lanczos eigenvalues of Q^2, ascending).
  * Converges each of the l+1 lowest Ritz values of Q^2 to relative residual tol. */
@@ -203,7 +212,7 @@ nd_status nd_lowmodes(nd_ctx* ctx, int l, double tol, int maxit, double* nu, dou
 
 /* Low modes with l chosen dynamically (Sec. 2.3): in [l_min, l_max] the l with the largest relative
  * gap (sqrt(lambda_{l+1}) - sqrt(lambda_l)) / sqrt(lambda_{l+1}) of the Q^2 Ritz values is taken, so
- * that the spectral distance of the kept modes from the rest is not accidentally small, and the
+ * that the kept modes are well separated from the remaining spectrum, and the
  * iteration stops when kappa_+ and kappa_- (as in nd_lowmodes) are both <= kappa_target.  The
  * projector deviation of Sec. 2.3 is then <= kappa (1 + 2 kappa) / (1 - 2 kappa (1 + 2 kappa)).
  * Outputs as nd_lowmodes with l = *l_out modes (host arrays sized for l_max, eval_Q2 for l_max + 1).
@@ -297,6 +306,14 @@ nd_status nd_apply_sign(nd_ctx* ctx, double* out_dev, const double* in_dev, cons
 /* out = D_N^m in, D_N = (1 + gamma5 sign(Q)) / abar, abar = 1/(1 + s)  (Sec. 2.2, 2.3). */
 nd_status nd_apply_DN(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p, nd_dn_info* info);
 
+/* out = (D_N^m)^dagger in = gamma5 D_N^m gamma5 in (Sec. 2.2: D_N is gamma5-hermitian because sign(Q) is
+ * hermitian), computed as (f + m_q) in + f sign(Q) gamma5 in with f = (1 - abar m_q / 2) / abar: one
+ * sign(Q) application, the multi-shift solves recomputed.  This is the vector-Jacobian product of
+ * in -> D_N^m in.  Exact for the two-sided approximation only: p->left_only = 1 returns
+ * ND_ERR_INVALID_ARG.  Arguments, deflation and info as nd_apply_DN. */
+nd_status nd_apply_DN_dagger(nd_ctx* ctx, double* out_dev, const double* in_dev, const nd_dn_params* p,
+                             nd_dn_info* info);
+
 /* ---------------------------------------------------------------- propagators */
 
 typedef struct {
@@ -321,7 +338,9 @@ nd_status nd_propagator(nd_ctx* ctx, double* x_dev, const double* b_dev, const n
 
 /* ---------------------------------------------------------------- differentiation */
 
-/* Force of S = phi^dagger (Q^2)^{-1} phi with respect to the links: F[mu][lex][a] =
+/* Force of S = phi^dagger (Q^2)^{-1} phi with respect to the links (derived from the definition of
+ * Q in Sec. 2.1: dS = -2 Re Y^dagger dQ X with X = (Q^2)^{-1} phi, Y = Q X; the paper has no force
+ * passage): F[mu][lex][a] =
  * dS/d omega for U_mu(x) -> exp(i omega T^a) U_mu(x), T^a = lambda^a/2 (F_dev: [4][V][8]
  * FP64, device).  X = (Q^2)^{-1} phi is recomputed by CG (inner precision as nd_solve) to
  * relative residual tol; the force itself is one FP64 pass over the links. */

@@ -108,9 +108,24 @@ def lowmodes_arpack(U, dims, m, l, antiperiodic_t=False, tol=1e-12):
     return {"nu": nu, "u": u, "rho": rho, "eval_Q2": w, "lam_next": float(w[l]), "lam_max": float(lam_max)}
 
 
+def lambda_max_arpack(U, dims, m, antiperiodic_t=False, tol=1e-8):
+    """Largest eigenvalue of Q^2 by ARPACK (scipy eigsh, which='LA') on the oracle's Q^2; the
+    upper end of the interval that X = Q / sqrt(lambda_max) is scaled to (Sec. 2.2)."""
+    import scipy.sparse.linalg as sla
+    V = int(np.prod(dims))
+    n = 12 * V
+    shape = (V, 4, 3)
+
+    def q2(v):
+        return wilson.apply_Q2(U, np.ascontiguousarray(v.reshape(shape)), dims, m, antiperiodic_t).reshape(-1)
+
+    op = sla.LinearOperator((n, n), matvec=q2, dtype=np.complex128)
+    return float(sla.eigsh(op, k=1, which="LA", tol=tol, return_eigenvectors=False)[0])
+
+
 def choose_l(evals_q2, l_min, l_max):
-    """Number of low modes to deflate (Sec. 2.3: chosen dynamically so that the spectral distance
-    to the remaining modes is not accidentally small).  Reading: among l_min <= l <= l_max take the
+    """Number of low modes to deflate (Sec. 2.3: l is chosen at run time so that the kept modes are
+    well separated from the rest of the spectrum).  Reading: among l_min <= l <= l_max take the
     l with the largest relative gap between the last kept and the first remaining mode of Q,
         g_l = (sqrt(lambda_{l+1}) - sqrt(lambda_l)) / sqrt(lambda_{l+1}),
     lambda_1 <= lambda_2 <= ... the eigenvalues of Q^2; the smallest such l on ties."""

@@ -94,6 +94,14 @@ def sign_apply_poly(U, dims, m, eta, lam_max, eps, degree, u=None, nu=None, two_
     return z, {"delta": coef["delta"], "degree": int(degree)}
 
 
+def dn_from_sign(eta, sign_eta, s, m_q=0.0):
+    """D_N^m eta from eta and sign(Q) eta (Sec. 2.2): D_N = (1 + gamma5 sign(Q)) / abar,
+    abar = 1 / (1 + s), and D_N^m = (1 - abar m_q/2) D_N + m_q."""
+    abar = 1.0 / (1.0 + s)
+    dn = (eta + gamma5(sign_eta)) / abar
+    return (1.0 - abar * m_q / 2.0) * dn + m_q * eta
+
+
 def dn_apply(U, dims, m, s, eta, lam_max, eps, npoles, tol, u=None, nu=None, m_q=0.0, two_sided=True,
              antiperiodic_t=False, degree=None):
     """D_N^m eta = (1 - abar m_q/2) (1 + s) (eta + gamma5 sign(Q) eta) + m_q eta.  With ``degree``
@@ -102,9 +110,7 @@ def dn_apply(U, dims, m, s, eta, lam_max, eps, npoles, tol, u=None, nu=None, m_q
         sg, info = sign_apply(U, dims, m, eta, lam_max, eps, npoles, tol, u, nu, two_sided, antiperiodic_t)
     else:
         sg, info = sign_apply_poly(U, dims, m, eta, lam_max, eps, degree, u, nu, two_sided, antiperiodic_t)
-    abar = 1.0 / (1.0 + s)
-    dn = (eta + gamma5(sg)) / abar
-    return (1.0 - abar * m_q / 2.0) * dn + m_q * eta, info
+    return dn_from_sign(eta, sg, s, m_q), info
 
 
 def propagator(U, dims, m, s, b, lam_max, eps, npoles, tol_inner, u=None, nu=None, m_q=0.1, tol=1e-10,

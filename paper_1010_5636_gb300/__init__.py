@@ -93,6 +93,7 @@ _SIGS = {
     "nd_chebyshev_degree": ([_D, _D, ctypes.POINTER(_I)], _I),
     "nd_apply_sign": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_apply_DN": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
+    "nd_apply_DN_dagger": ([_P, _P, _P, ctypes.POINTER(nd_dn_params), ctypes.POINTER(nd_dn_info)], _I),
     "nd_force": ([_P, _P, _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
     "nd_link_gradient": ([_P, _P, _P, ctypes.POINTER(_D), _P, _D, _I, _I, ctypes.POINTER(nd_solve_info)], _I),
 }
@@ -375,6 +376,14 @@ def nd_apply_DN(ctx, out, inp, params):
     info = nd_dn_info()
     _check(ctx, lib().nd_apply_DN(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params), ctypes.byref(info)),
            "nd_apply_DN")
+    return info
+
+
+def nd_apply_DN_dagger(ctx, out, inp, params):
+    """out = (D_N^m)^dagger inp = gamma5 D_N^m gamma5 inp (two-sided sign(Q) only)."""
+    info = nd_dn_info()
+    _check(ctx, lib().nd_apply_DN_dagger(ctx, _ptr(_f64(out)), _ptr(_f64(inp)), ctypes.byref(params),
+                                         ctypes.byref(info)), "nd_apply_DN_dagger")
     return info
 
 

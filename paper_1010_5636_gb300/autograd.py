@@ -11,20 +11,14 @@ nd_apply_DN), all arithmetic runs in the library's kernels.
   U = matrix_exp(i omega.T) @ U0) is differentiated through by torch, so dS/domega at omega = 0
   is the su(3) force of nd_force.
 * ``dirac_overlap(lat, eta, params)`` -> D_N eta (Sec. 2.2), differentiable in the source: the
-  vector-Jacobian product is D_N^dagger g = gamma5 D_N gamma5 g, exact for the two-sided deflated
-  sign (hermitian); the multi-shift solves are recomputed rather than stored.
+  vector-Jacobian product is D_N^dagger g = gamma5 D_N gamma5 g (nd_apply_DN_dagger), exact for the
+  two-sided deflated sign (hermitian); the multi-shift solves are recomputed rather than stored.
 """
 import torch
 
-from . import ND_FP64, dn_params, nd_apply_DN, nd_link_gradient, nd_set_links
+from . import ND_FP64, dn_params, nd_apply_DN, nd_apply_DN_dagger, nd_link_gradient, nd_set_links
 
-__all__ = ["pseudofermion_action", "dirac_overlap", "PseudofermionAction", "DiracOverlap", "gamma5"]
-
-
-def gamma5(psi):
-    """gamma5 = diag(1, 1, -1, -1) on canonical spinors [..., V, 4, 3]."""
-    s = torch.tensor([1.0, 1.0, -1.0, -1.0], dtype=torch.float64, device=psi.device)
-    return psi * s.view(4, 1)
+__all__ = ["pseudofermion_action", "dirac_overlap", "PseudofermionAction", "DiracOverlap"]
 
 
 class PseudofermionAction(torch.autograd.Function):
@@ -64,11 +58,9 @@ class DiracOverlap(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, g):
-        if ctx.params.left_only:
-            raise RuntimeError("the VJP of D_N is gamma5 D_N gamma5 only for the two-sided (hermitian) sign")
         out = torch.empty_like(g)
-        nd_apply_DN(ctx.lat.ctx, out, gamma5(g.contiguous()).contiguous(), ctx.params)
-        return gamma5(out), None, None
+        nd_apply_DN_dagger(ctx.lat.ctx, out, g.contiguous(), ctx.params)
+        return out, None, None
 
 
 def dirac_overlap(lat, eta, params=None):

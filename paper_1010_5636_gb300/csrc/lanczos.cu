@@ -534,7 +534,7 @@ extern "C" nd_status nd_lowmode_state(nd_ctx* c, int* l, double* lambda_next, do
 // The block iteration above runs for l_max + 1 wanted modes.  After each step the candidate l in
 // [l_min, l_max] with the largest relative gap (sqrt(theta_{l+1}) - sqrt(theta_l)) / sqrt(theta_{l+1})
 // between the last kept and the first remaining Ritz value of Q^2 is taken (smallest l on ties), so
-// that the spectral distance d_k entering kappa is not accidentally small.  Once the l + 1 lowest
+// that the spectral distance d_k entering kappa is not small by chance.  Once the l + 1 lowest
 // Q^2 residuals are below 1e-4 lambda_max, the Rayleigh-Ritz pairs of Q on the first l vectors give
 // rho_k and kappa_+- (d_k as in nd_lowmodes, lambda_{l+1} ~ theta_{l+1}); the iteration stops when
 // both kappas are at most kappa_target.  Once all candidates' Ritz values have settled, l is

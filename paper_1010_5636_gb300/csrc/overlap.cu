@@ -231,3 +231,32 @@ extern "C" nd_status nd_apply_DN(nd_ctx* c, double* out, const double* in, const
   if (info) info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   return ND_OK;
 }
+
+// D_N^m^dagger eta = gamma5 D_N^m gamma5 eta (Sec. 2.2: D_N^dagger = gamma5 D_N gamma5 because sign(Q) is
+// hermitian; the two-sided deflated approximation keeps it so).  With f = (1 - abar m_q/2)(1 + s):
+//   gamma5 [f (gamma5 eta + gamma5 sign(Q) gamma5 eta) + m_q gamma5 eta] = (f + m_q) eta + f sign(Q) gamma5 eta,
+// so one sign(Q) application on gamma5 eta and one combination.
+extern "C" nd_status nd_apply_DN_dagger(nd_ctx* c, double* out, const double* in, const nd_dn_params* p,
+                                        nd_dn_info* info) {
+  if (!c) return ND_ERR_INVALID_ARG;
+  if (!out || out == in || !p) return fail(c, ND_ERR_INVALID_ARG, "nd_apply_DN_dagger: bad argument");
+  if (p->left_only)
+    return fail(c, ND_ERR_INVALID_ARG, "nd_apply_DN_dagger: gamma5 D_N gamma5 is the adjoint only of the two-sided form");
+  if (c->poisoned) return fail(c, ND_ERR_STATE, "context unusable after an earlier CUDA error: " + c->err);
+  auto t0 = std::chrono::steady_clock::now();
+  void* eta = field(c, "dnd_eta", 0);
+  void* g5eta = field(c, "dnd_g5eta", 0);
+  void* o = field(c, "dn_out", 0);
+  if (!eta || !g5eta || !o) return fail(c, ND_ERR_OOM, "nd_apply_DN_dagger: workspace");
+  ND_TRY(nd_pack_spinor(c, eta, in, ND_FP64, 1));
+  ND_TRY_CUDA(c, blas_g5(c->g, 0, g5eta, eta, c->stream));
+  void *sg, *e2;
+  ND_TRY(sign_impl(c, static_cast<const double*>(g5eta), p, info, &sg, &e2, true));
+  const double abar = 1.0 / (1.0 + c->s);
+  const double f = (1.0 - 0.5 * abar * p->m_q) / abar;
+  ND_TRY_CUDA(c, blas_axpby(c->g, 0, o, f + p->m_q, eta, f, sg, false, slot(c, nullptr), c->stream));
+  ND_TRY(nd_unpack_spinor(c, out, o, ND_FP64, 1));
+  ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (info) info->time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return ND_OK;
+}

@@ -110,3 +110,28 @@ def test_overlap_vjp(nd):
     loss.backward()
     # torch's gradient of the real loss Re <w, A eta> with respect to eta is A^H w
     assert rel(host(e.grad), expect) <= 1e-10
+
+
+def test_dn_dagger_massive(nd):
+    """nd_apply_DN_dagger: (D_N^m)^dagger w = gamma5 D_N^m gamma5 w (oracle) for m_q > 0, and the
+    left-only form (not hermitian) is refused."""
+    import torch
+    dims = (2, 2, 2, 2)
+    U = synth.gauge_field(dims, "haar", seed=0)
+    lm = lowmodes.lowmodes_dense(U, dims, M, 6)
+    lam_max = 1.01 * lm["lam_max"]
+    eps = 0.99 * lm["lam_next"] / lam_max
+    w = synth.spinor(dims, seed=2)
+    expect, _ = overlap.dn_apply(U, dims, M, S, overlap.gamma5(w), lam_max, eps, 16, 1e-12, lm["u"], lm["nu"],
+                                 m_q=0.1)
+    expect = overlap.gamma5(expect)
+    lat = nd.Lattice(dims, U=dev(U), m=M, s=S, recon=(18, 12, 12))
+    nd.nd_set_lowmodes(lat.ctx, dev(lm["u"]), list(lm["nu"]), lm["lam_next"])
+    out = torch.empty_like(dev(w))
+    for inner in (0, 1):
+        nd.nd_apply_DN_dagger(lat.ctx, out, dev(w), nd.dn_params(16, eps, lam_max, 1e-12, 100000, inner, 0.1))
+        assert rel(host(out), expect) <= 1e-10
+    with pytest.raises(nd.NdError) as e:
+        nd.nd_apply_DN_dagger(lat.ctx, out, dev(w), nd.dn_params(16, eps, lam_max, 1e-12, 100000, 0, 0.1, True))
+    assert e.value.status == nd.ND_ERR_INVALID_ARG
+    lat.close()

@@ -174,6 +174,15 @@ def test_Q_full_size_fp32(nd, dims):
     assert _q_case(nd, dims, "near_identity", 1, 8) <= TOL[1]
 
 
+@pytest.mark.parametrize("recon", [18, 12, 8])
+def test_Q_full_size_fp16(nd, recon):
+    """FP16 storage with a per-site FP32 scale on the 24^3 x 48 sweep lattice.  No parity threshold
+    is set for this form; its error against the oracle is printed and held to 2e-3."""
+    err = _q_case(nd, (48, 24, 24, 24), "near_identity", 2, recon)
+    print(f"FP16-{recon} Q on 24^3 x 48: relative L2 error {err:.2e} vs the oracle")
+    assert err <= TOL[2], err
+
+
 def test_Q_full_size_fp64(nd):
     assert _q_case(nd, (64, 32, 32, 32), "near_identity", 0, 18) <= TOL[0]
 

@@ -23,6 +23,18 @@ def test_arpack_matches_dense():
     assert np.max(ar["rho"]) < 1e-8
 
 
+def test_lambda_max_arpack_matches_dense():
+    dims = (4, 4, 2, 4)
+    U = synth.gauge_field(dims, "haar", seed=0)
+    de = lowmodes.lowmodes_dense(U, dims, M, 1)
+    lm = lowmodes.lambda_max_arpack(U, dims, M, tol=1e-10)
+    assert abs(lm - de["lam_max"]) <= 1e-8 * de["lam_max"]
+    # free field: the largest Q^2 eigenvalue is the closed form max_p (m + sum(1 - cos p))^2 + sum sin^2 p,
+    # reached at p = (pi, pi, pi, pi): (m + 8)^2
+    Uf = synth.gauge_field(dims, "unit")
+    assert abs(lowmodes.lambda_max_arpack(Uf, dims, M, tol=1e-10) - (M + 8.0) ** 2) <= 1e-8 * (M + 8.0) ** 2
+
+
 def test_choose_l_rule():
     # eigenvalues of Q^2 with one clear relative gap after the 5th mode
     ev = np.array([0.01, 0.011, 0.0112, 0.0113, 0.0115, 0.05, 0.051, 0.052, 0.06, 0.061])

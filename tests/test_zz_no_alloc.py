@@ -1,7 +1,8 @@
 """The allocation-free Q with fused norms (nd_apply_Q_norms_static), for callers that may not
 call cudaMalloc at call time: its output must equal nd_apply_Q's and its norms the norms of
 the two fields, on two calls in a row (the second call reuses the static scratch that the
-first one left behind).  Collected last on purpose."""
+first one left behind), and the second call must leave the device's free memory unchanged.
+Collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -28,7 +29,14 @@ def test_static_norms_match_existing_entry_point(prec, tol):
             ref = torch.empty_like(a)
             nd.nd_apply_Q(ctx, ref, a, prec)
             out = torch.empty_like(a)
+            torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
             n_out, n_in = nd.nd_apply_Q_norms_static(ctx, out, a, prec)
+            torch.cuda.synchronize()
+            if call == 1:
+                # the first call may load the module and look up the array's address; the second must
+                # leave the device's free memory exactly as it was (no allocation of any kind)
+                assert torch.cuda.mem_get_info()[0] == free_before
             V = int(np.prod(dims))
             got_c = torch.empty((V, 4, 3), dtype=torch.complex128, device="cuda")
             ref_c = torch.empty_like(got_c)
