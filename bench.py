@@ -353,9 +353,20 @@ def dslash_phase(nd, torch, steps, warm, world, clocks):
             "e2e_gbs": e2e_gbs, "io_bytes": nbytes_io, "launches": 2 * steps, "V": V}
 
 
-def sweep_phase(nd, torch):
-    """Bandwidth sweep: every precision x link form, full fused Q and the one-parity pass (median of
-    10 launches with a 512 MB write between launches to flush L2)."""
+SWEEP_DIMS = ((64, 32, 32, 32), (48, 24, 24, 24), (32, 16, 16, 16))
+
+
+def sweep_phase(nd, torch, dims_list=SWEEP_DIMS):
+    """Bandwidth sweep over the three lattices of the Wilson-Dirac sweep: every precision x link form,
+    full fused Q and the one-parity pass (median of 10 launches with a 512 MB write between launches
+    to flush L2; 16^3x32 fits in L2 without the flush, so its numbers are those of a cold L2)."""
+    out = []
+    for dims in dims_list:
+        out += sweep_lattice(nd, torch, dims)
+    return out
+
+
+def sweep_lattice(nd, torch, DIMS):
     import numpy as np
 
     import synth
@@ -391,7 +402,7 @@ def sweep_phase(nd, torch):
                 t = float(np.median(ts)) * 1e-3
                 sites = V // 2 if half else V
                 gbs = sites * site_bytes(prec, recon, half) / t / 1e9
-                out.append({"prec": ["fp64", "fp32", "fp16"][prec], "recon": recon,
+                out.append({"lattice": f"{DIMS[1]}^3x{DIMS[0]}", "prec": ["fp64", "fp32", "fp16"][prec], "recon": recon,
                             "kernel": "half" if half else "full_Q", "us": round(t * 1e6, 1),
                             "GB/s": round(gbs, 1), "Gsite/s": round(sites / t / 1e9, 3)})
             del a, b
@@ -399,8 +410,83 @@ def sweep_phase(nd, torch):
     return out
 
 
-def dn_phase(nd, torch, reps):
-    """D_N applies/s: 16^3x32 Haar links, 20 poles, 20 FP64 Lanczos modes, rational part to 1e-10."""
+SPINOR_SITE_BYTES = {0: 192, 1: 96, 2: 52}
+
+
+def krylov_roofline(info, ps, px, ymode, recon, V, peak):
+    """Algorithmic HBM bytes of the multi-shift pass the library ran (from its work counters) over its
+    device time.  Per iteration and site: two full Q launches (t = Q p_0; r -= alpha (a Q t + sigma_0 p_0)
+    also reads p_0 and r), the update kernel's read of r, and per shift the read and write of p_l (every
+    live shift) and of x_l (every active shift; with only y = sum_l b_l x_l kept, one read and write of y
+    per iteration instead)."""
+    sb, sx = SPINOR_SITE_BYTES[ps], SPINOR_SITE_BYTES[px]
+    per_iter = 2 * site_bytes(ps, recon, half=False) + 3 * sb + (2 * sx if ymode else 0)
+    total = V * (info.iters * per_iter + info.krylov_live_shifts * 2 * sb +
+                 (0 if ymode else info.krylov_active_shifts * 2 * sx))
+    t = info.krylov_ms * 1e-3
+    ach = total / t / 1e9 if t > 0 else None
+    return {"bound": "hbm", "achieved": round(ach, 1) if ach else None, "peak": peak, "unit": "GB/s",
+            "frac": round(ach / peak, 4) if ach else None, "bytes_per_iteration_per_site":
+            round(total / max(1, info.iters) / V, 1), "iterations": info.iters,
+            "live_shift_iterations": info.krylov_live_shifts, "active_shift_iterations": info.krylov_active_shifts,
+            "pass_ms": round(info.krylov_ms, 3), "us_per_iteration": round(1e3 * info.krylov_ms / max(1, info.iters), 2),
+            "traffic": None}
+
+
+def dn_oracle_check(nd, torch, reps, peak):
+    """Per-vector error against the FP64 oracle on the mixed-precision workload's lattice (16^3x32 Haar,
+    seed 0, source seed 1, 20 poles, rational part to 1e-10), undeflated on the explicit interval
+    [eps, 1] = [1e-3, 1] with lambda_max from the oracle (ARPACK, padded by 1 %): both sides take the
+    same interval, and eps lies below lambda_min / lambda_max of this field.  Also times these D_N
+    applies (FP64, mixed FP32, mixed FP16) with their multi-shift rooflines."""
+    import numpy as np
+
+    import synth
+    from oracle import lowmodes, overlap, wilson
+    cores = len(os.sched_getaffinity(0))
+    wilson.set_threads(cores)
+    Uh = synth.gauge_field(DN_DIMS, "haar", seed=0)
+    etah = synth.spinor(DN_DIMS, seed=1)
+    t0 = time.perf_counter()
+    lam_max = 1.01 * lowmodes.lambda_max_arpack(Uh, DN_DIMS, -1.4)
+    sg, oinfo = overlap.sign_apply(Uh, DN_DIMS, -1.4, etah, lam_max, 1e-3, 20, 1e-12)
+    ref = overlap.dn_from_sign(etah, sg, 0.4)
+    t_or = time.perf_counter() - t0
+    V = int(np.prod(DN_DIMS))
+    ctx = nd.nd_create(DN_DIMS, m=-1.4, s=0.4)
+    nd.nd_set_links(ctx, torch.from_numpy(Uh).cuda(), (18, RECON, RECON))
+    eta = torch.from_numpy(etah).cuda()
+    res = {"workload": f"D_N on {DN_DIMS[1]}^3x{DN_DIMS[0]} Haar links (seed 0), 20 poles, undeflated, eps 1e-3, "
+                       f"lambda_max {lam_max:.4f} (oracle ARPACK x 1.01), rational part to 1e-10",
+           "oracle_s": round(t_or, 1), "oracle_cores": wilson.get_threads(), "oracle_krylov_iters": oinfo["iters"]}
+    for name, inner in (("fp64", 0), ("mixed_fp32", 1), ("mixed_fp16", 2)):
+        p = nd.dn_params(20, 1e-3, lam_max, 1e-10, 200000, inner)
+        o = torch.empty_like(eta)
+        nd.nd_apply_DN(ctx, o, eta, p)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            t1 = time.perf_counter()
+            info = nd.nd_apply_DN(ctx, o, eta, p)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t1)
+        t = float(np.median(ts))
+        got = o.cpu().numpy()
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        res[name] = {"rel_err_vs_oracle": err, "applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4),
+                     "krylov_iters": info.iters, "refinement_sweeps": info.outer,
+                     "residuals64": info.residuals64, "correction_iters": info.correction_iters,
+                     "refine_ms": round(info.refine_ms, 2),
+                     "krylov_roofline": krylov_roofline(info, inner, 0 if inner == 0 else 1, inner == 0,
+                                                        18 if inner == 0 else RECON, V, peak)}
+    for name in ("mixed_fp32", "mixed_fp16"):
+        res[name]["speedup_vs_fp64"] = round(res["fp64"]["s_per_apply"] / res[name]["s_per_apply"], 3)
+    nd.nd_destroy(ctx)
+    return res
+
+
+def dn_phase(nd, torch, reps, peak):
+    """D_N applies/s: 16^3x32 Haar links, 20 poles, 20 deflated low modes, rational part to 1e-10."""
     import numpy as np
 
     import synth
@@ -433,7 +519,11 @@ def dn_phase(nd, torch, reps):
         outs[name] = o.clone()
         res[name] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "krylov_iters": info.iters,
                      "sloppy_iters": info.sloppy_iters, "refinement_sweeps": info.outer,
-                     "max_shift_resid": info.max_resid, "delta_zolotarev": info.delta, "eps": info.eps}
+                     "max_shift_resid": info.max_resid, "delta_zolotarev": info.delta, "eps": info.eps,
+                     "residuals64": info.residuals64, "correction_iters": info.correction_iters,
+                     "refine_ms": round(info.refine_ms, 2),
+                     "krylov_roofline": krylov_roofline(info, inner, 0 if inner == 0 else 1, inner == 0,
+                                                        18 if inner == 0 else RECON, int(np.prod(DN_DIMS)), peak)}
     # the paper's own approximation: minmax polynomial of the smallest degree with delta <= 1e-10,
     # Clenshaw recurrence in FP64 or FP32 (no refinement)
     for name, inner in (("poly_fp64", 0), ("poly_fp32", 1)):
@@ -554,6 +644,22 @@ def profile_case(nd, torch, case):
         nd.nd_set_links(ctx, U, (18, RECON, 0))
         o = torch.empty_like(eta)
         nd.nd_apply_sign(ctx, o, eta, nd.dn_params(0, 0.01, 30.0, 1e-10, 1, 1, approx=nd.ND_SIGN_CHEBYSHEV, degree=4))
+        torch.cuda.synchronize()
+        nd.nd_destroy(ctx)
+    elif case in ("dn16", "dn16_fp64", "dn16_fp16"):
+        # one D_N apply on 16^3x32 Haar links, 20 poles, undeflated on [1e-3, 1] with lambda_max = 30.2
+        # (above the largest Q^2 eigenvalue of this field, 29.9), rational part to 1e-10: mixed FP32,
+        # FP64 or mixed FP16 inner solves, about 1 GB on the device.  The Krylov iterations run as
+        # host-issued launches (ND_GRAPHS=0) so that a profiler sees every kernel.
+        os.environ["ND_GRAPHS"] = "0"
+        dims = (32, 16, 16, 16)
+        U = torch.from_numpy(synth.gauge_field(dims, "haar", seed=0)).cuda()
+        eta = torch.from_numpy(synth.spinor(dims, seed=1)).cuda()
+        ctx = nd.nd_create(dims, m=-1.4, s=0.4)
+        nd.nd_set_links(ctx, U, (18, RECON, RECON))
+        inner = {"dn16": 1, "dn16_fp64": 0, "dn16_fp16": 2}[case]
+        o = torch.empty_like(eta)
+        nd.nd_apply_DN(ctx, o, eta, nd.dn_params(20, 1e-3, 30.2, 1e-10, 200000, inner))
         torch.cuda.synchronize()
         nd.nd_destroy(ctx)
     else:
@@ -681,6 +787,51 @@ def force_phase(nd, torch, reps=2):
     return res
 
 
+def vjp_phase(nd, torch, reps=2):
+    """Source VJP of D_N on 16^4 near-identity links (eps 0.3, seed 0; the differentiation workload):
+    torch.autograd through DiracOverlap, forward D_N eta, backward D_N^dagger g = gamma5 D_N gamma5 g
+    (nd_apply_DN_dagger: one sign(Q) on gamma5 g with the multi-shift solves recomputed).  Nothing of
+    the forward pass serves a new source, so the backward costs one more D_N apply; keeping the
+    forward's 20 shifted solutions instead would hold 20 x V x 24 FP64 reals (252 MB) for no reuse.
+    8 deflated low modes, 20 poles, rational part to 1e-10, FP64 and mixed FP32 inner solves."""
+    import numpy as np
+
+    import synth
+    from paper_1010_5636_gb300 import autograd as ag
+    dims = (16, 16, 16, 16)
+    U = torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda()
+    lat = nd.Lattice(dims, U=U, m=-1.4, s=0.4, recon=(18, RECON, RECON))
+    t0 = time.perf_counter()
+    _, _, _, li = nd.nd_lowmodes(lat.ctx, 8, LOWMODE_TOL, 2000000)
+    res = {"workload": "D_N source VJP on 16^4 near-identity links eps=0.3, 8 deflated modes, 20 poles, 1e-10",
+           "lowmodes_s": round(time.perf_counter() - t0, 3), "kappa_plus": li.kappa_plus, "kappa_minus": li.kappa_minus}
+    eta = torch.from_numpy(synth.spinor(dims, seed=1)).cuda()
+    w = torch.from_numpy(synth.spinor(dims, seed=2)).cuda()
+    for name, inner in (("fp64", 0), ("mixed_fp32", 1)):
+        p = nd.dn_params(20, 0.0, 0.0, 1e-10, 200000, inner)
+        tf, tb = [], []
+        for _ in range(reps + 1):
+            e = eta.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            out = ag.dirac_overlap(lat, e, p)
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            loss = (torch.conj(w) * out).real.sum()
+            loss.backward()
+            torch.cuda.synchronize()
+            t3 = time.perf_counter()
+            tf.append(t2 - t1)
+            tb.append(t3 - t2)
+        # <w, D eta> = <D^dagger w, eta>: the gradient of Re<w, D eta> is D^dagger w
+        lhs = complex(torch.vdot(w.reshape(-1), out.detach().reshape(-1)))
+        rhs = complex(torch.vdot(e.grad.reshape(-1), eta.reshape(-1)))
+        res[name] = {"forward_s": round(float(np.median(tf[1:])), 4), "backward_s": round(float(np.median(tb[1:])), 4),
+                     "adjoint_identity_rel": abs(lhs - rhs) / abs(lhs)}
+    lat.close()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -691,8 +842,11 @@ def main():
     ap.add_argument("--no-dn", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the multi-RHS and force measurements")
     ap.add_argument("--dn-reps", type=int, default=2)
+    ap.add_argument("--no-oracle-dn", action="store_true",
+                    help="skip the D_N comparison with the FP64 oracle (about a minute of host time)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--case", default=None, help="run a small profiling case and exit (hop24, clen24)")
+    ap.add_argument("--case", default=None,
+                    help="run a small profiling case and exit (hop24, clen24, dn16, dn16_fp64, dn16_fp16)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -748,11 +902,14 @@ def main():
     if not args.no_sweep:
         line["sweep"] = sweep_phase(nd, torch)
     if not args.no_dn:
-        line["dn"] = dn_phase(nd, torch, args.dn_reps)
+        line["dn"] = dn_phase(nd, torch, args.dn_reps, peak)
+        if not args.no_oracle_dn:
+            line["dn"]["oracle_check"] = dn_oracle_check(nd, torch, args.dn_reps, peak)
         line["clenshaw"] = clenshaw_phase(nd, torch)
     if not args.no_extra:
         line["multi_rhs"] = mrhs_phase(nd, torch)
         line["force"] = force_phase(nd, torch)
+        line["vjp"] = vjp_phase(nd, torch)
     if rank == 0 and world == 1:
         line["cpu_baseline"] = oracle_baseline(args.cpu_seconds)
     if rank == 0:

@@ -294,6 +294,14 @@ typedef struct {
   double max_resid;    /* max over shifts of the FP64 relative residual of the shifted solves */
   double time_ms;
   int degree;          /* ND_SIGN_CHEBYSHEV: degree of P_n used (Clenshaw iterations); else 0 */
+  /* work and time of the multi-shift pass (the sloppy pass in mixed precision), for byte counts: */
+  double krylov_ms;          /* device time of its iterations (CUDA events on the context's stream) */
+  int krylov_live_shifts;    /* sum over its iterations of the shifts whose direction p_l was updated */
+  int krylov_active_shifts;  /* sum over its iterations of the shifts whose solution term was updated */
+  /* the FP64 defect correction (mixed precision; 0 otherwise): */
+  int residuals64;           /* FP64 residuals b - (X^2 + sigma_l) x_l computed */
+  int correction_iters;      /* iterations of the correction solves, summed over systems */
+  double refine_ms;          /* wall time of the refinement */
 } nd_dn_info;
 
 /* out = sign(Q) in with the deflated approximation

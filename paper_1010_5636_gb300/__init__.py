@@ -49,7 +49,9 @@ class nd_dn_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("sloppy_iters", ctypes.c_int), ("outer", ctypes.c_int),
                 ("n_low", ctypes.c_int), ("delta", ctypes.c_double), ("eps", ctypes.c_double),
                 ("lambda_max", ctypes.c_double), ("max_resid", ctypes.c_double), ("time_ms", ctypes.c_double),
-                ("degree", ctypes.c_int)]
+                ("degree", ctypes.c_int), ("krylov_ms", ctypes.c_double), ("krylov_live_shifts", ctypes.c_int),
+                ("krylov_active_shifts", ctypes.c_int), ("residuals64", ctypes.c_int),
+                ("correction_iters", ctypes.c_int), ("refine_ms", ctypes.c_double)]
 
 
 class nd_prop_info(ctypes.Structure):

@@ -93,6 +93,44 @@ __global__ void __launch_bounds__(B_THREADS) convert_kernel(const Geom g, void* 
   SpinorIO<PO>::store(w, out, g.Vh, p, h);
 }
 
+// out (precision PO) = in (FP64) / sqrt(*norm2); zero when *norm2 is zero
+template <int PO>
+__global__ void __launch_bounds__(B_THREADS) convert_normalized_kernel(const Geom g, void* out, const void* in,
+                                                                        const double* norm2) {
+  using TO = typename Traits<PO>::real;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= blas_sites(g)) return;
+  int p, h;
+  site_ph(g, i, &p, &h);
+  const double n2 = *norm2;
+  const double sc = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  Spinor<double> v;
+  SpinorIO<P64>::load(v, in, g.Vh, p, h);
+  Spinor<TO> w;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w.s[k][c] = mk((TO)(sc * v.s[k][c].re), (TO)(sc * v.s[k][c].im));
+  SpinorIO<PO>::store(w, out, g.Vh, p, h);
+}
+
+// x (FP64) += a e (e FP32)
+__global__ void __launch_bounds__(B_THREADS) axpy_widen_kernel(const Geom g, void* x, double a, const void* e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= blas_sites(g)) return;
+  int p, h;
+  site_ph(g, i, &p, &h);
+  Spinor<double> vx;
+  Spinor<float> ve;
+  SpinorIO<P64>::load(vx, x, g.Vh, p, h);
+  SpinorIO<P32>::load(ve, e, g.Vh, p, h);
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vx.s[k][c] = vx.s[k][c] + a * mk((double)ve.s[k][c].re, (double)ve.s[k][c].im);
+  SpinorIO<P64>::store(vx, x, g.Vh, p, h);
+}
+
 __global__ void __launch_bounds__(B_THREADS) g5_axpby_kernel(const Geom g, void* out, double c1, const void* x,
                                                               double c2, const void* y) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -216,6 +254,21 @@ cudaError_t blas_convert(const Geom& g, int po, void* out, int pi, const void* i
   CV(P64, P64) CV(P64, P32) CV(P64, P16) CV(P32, P64) CV(P32, P32) CV(P32, P16) CV(P16, P64) CV(P16, P32) CV(P16, P16)
 #undef CV
   return cudaErrorInvalidValue;
+}
+
+cudaError_t blas_convert_normalized(const Geom& g, int po, void* out, const void* in, const double* norm2,
+                                    cudaStream_t st) {
+  switch (po) {
+    case P32: convert_normalized_kernel<P32><<<nblocks(g), B_THREADS, 0, st>>>(g, out, in, norm2); break;
+    case P16: convert_normalized_kernel<P16><<<nblocks(g), B_THREADS, 0, st>>>(g, out, in, norm2); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t blas_axpy_widen(const Geom& g, void* x64, double a, const void* e32, cudaStream_t st) {
+  axpy_widen_kernel<<<nblocks(g), B_THREADS, 0, st>>>(g, x64, a, e32);
+  return cudaGetLastError();
 }
 
 cudaError_t blas_g5_axpby(const Geom& g, void* out, double c1, const void* x, double c2, const void* y,

@@ -1,6 +1,7 @@
 // C-ABI entry points of libnd: context lifecycle, field packing, site tables and Q.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -111,13 +112,17 @@ nd_status nd_create(nd_ctx** out, const int dims[4], int antiperiodic_t, double 
   g.Vh = (int)c->Vh;
   g.apbc = antiperiodic_t ? 1 : 0;
   g.even_only = 0;
+  // ND_GRAPHS=0: run the Krylov iterations as host-issued launches instead of captured graphs (a
+  // profiler cannot see the kernel nodes of a graph with a conditional while-loop)
+  if (const char* e = std::getenv("ND_GRAPHS")) c->graphs_ok = std::atoi(e) != 0;
   c->max_blocks = (int)((V + 15) / 16) + 1024;  // >= blocks of any reducing launch (64 sites per block at least)
   bool ok = cudaMalloc(&c->red_partials, sizeof(double) * 8 * c->max_blocks) == cudaSuccess &&
             cudaMalloc(&c->red_counter, sizeof(unsigned) * 16) == cudaSuccess &&
             cudaMalloc(&c->red_scratch, sizeof(double) * 64) == cudaSuccess &&
             cudaMallocHost(&c->host_pinned, sizeof(double) * ND_PINNED_DOUBLES) == cudaSuccess &&
             cudaMemset(c->red_counter, 0, sizeof(unsigned) * 16) == cudaSuccess &&
-            cudaMemset(c->red_scratch, 0, sizeof(double) * 64) == cudaSuccess;
+            cudaMemset(c->red_scratch, 0, sizeof(double) * 64) == cudaSuccess &&
+            cudaEventCreate(&c->ev[0]) == cudaSuccess && cudaEventCreate(&c->ev[1]) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     nd_destroy(c);
@@ -143,6 +148,8 @@ void nd_destroy(nd_ctx* c) {
   if (c->red_counter) cudaFree(c->red_counter);
   if (c->red_scratch) cudaFree(c->red_scratch);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  for (auto& e : c->ev)
+    if (e) cudaEventDestroy(e);
   cudaGetLastError();
   delete c;
 }

@@ -30,6 +30,7 @@ struct nd_ctx {
   double m = 0, s = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};  // device timing of solver passes (reported in info structs)
   // links per precision (index nd_prec); recon 0 = absent
   void* links[3] = {nullptr, nullptr, nullptr};
   int recon[3] = {0, 0, 0};
@@ -49,7 +50,8 @@ struct nd_ctx {
   size_t evecs_cap = 0;
   std::vector<double> nu, rho;
   double lam_next = 0.0, lam_max = 0.0;
-  // captured multi-shift iterations (graphs_ok = false after a capture failure: chunked launches)
+  // captured multi-shift iterations (graphs_ok = false after a capture failure, or with ND_GRAPHS=0 in
+  // the environment: chunked launches from the host)
   cudaStream_t cap_stream = nullptr;
   std::vector<nd_ms_graph> ms_graphs;
   bool graphs_ok = true;

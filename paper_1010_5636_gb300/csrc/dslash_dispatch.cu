@@ -37,9 +37,23 @@ cudaError_t launch_q_mrhs(const Geom& g, const QLaunch& L0, int nrhs, size_t str
   return launch_q(g, L, st);
 }
 
+// Right-hand sides per thread for multi-RHS launches the autotuner has not set; ND_Q_KRHS=1|2|3
+// in the environment overrides it (comparison measurements).
+static int default_krhs() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("ND_Q_KRHS");
+    v = e ? std::atoi(e) : 1;
+    if (v < 1 || v > 3) v = 1;
+  }
+  return v;
+}
+
 cudaError_t launch_q(const Geom& g, const QLaunch& L0, cudaStream_t st) {
   if (L0.nsites <= 0) return cudaSuccess;
   QLaunch L = L0;
+  if (L.mode == Q_MRHS && L.krhs == 0) L.krhs = default_krhs();
+  if (L.mode == Q_MRHS && L.krhs > 1 && L.prec != 0 && L.nrhs > 1) return launch_q_mrhs_k(g, L, st);
   if (L.mode == Q_MRHS && (L.nrhs < 1 || L.reduce)) return cudaErrorInvalidValue;
   if ((L.mode == Q_BPLAIN || L.mode == Q_BCG) && (L.nrhs < 1 || !L.reduce)) return cudaErrorInvalidValue;
   if (L.split == 0) L.split = default_split(L.prec, L.recon, L.nsites != 2 * g.Vh);

@@ -86,11 +86,10 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
     p = A.parity0;
     h = i;
   }
+  Site s;
+  if (act) s = site_of(g, p, h);
   Spinor<T> acc;
-  if (act) {
-    const Site s = site_of(g, p, h);
-    hopping_part<P, R, SPLIT>(acc, g, s, p, h, static_cast<const char*>(A.links), A.in, part);
-  }
+  if (act) hopping_part<P, R, SPLIT>(acc, g, s, p, h, static_cast<const char*>(A.links), A.in, part);
   if constexpr (SPLIT > 1) {
     extern __shared__ __align__(16) unsigned char qsm_raw[];
     T* sm = reinterpret_cast<T*>(qsm_raw);  // [SPLIT][24][SITES]
@@ -218,12 +217,18 @@ constexpr int q_min_blocks() {
   return (P == P32 && R == 18) ? 6 : 8;
 }
 
+// One warp per site in 64-thread blocks.
+template <int P, int R, int MODE, bool REDUCE>
+static cudaError_t launch_q64(const Geom& g, const QLaunch& L, cudaStream_t st) {
+  return launch_q5<P, R, MODE, REDUCE, 1, 64, q_min_blocks<P, R>()>(g, L, st);
+}
+
 template <int P, int R, int MODE, bool REDUCE>
 static cudaError_t launch_q4(const Geom& g, const QLaunch& L, cudaStream_t st) {
   switch (L.split) {
     case 1:
       if (P == P64 || L.threads == 256) return launch_q5<P, R, MODE, REDUCE, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, MODE, REDUCE, 1, 64, q_min_blocks<P, R>()>(g, L, st);
+      return launch_q64<P, R, MODE, REDUCE>(g, L, st);
     case 2: return launch_q5<P, R, MODE, REDUCE, 2, 256, 1>(g, L, st);
     case 4: return launch_q5<P, R, MODE, REDUCE, 4, 256, 1>(g, L, st);
   }
@@ -246,7 +251,7 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
     case Q_MRHS:
       if (L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64 || L.threads == 256) return launch_q5<P, R, Q_MRHS, false, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, Q_MRHS, false, 1, 64, q_min_blocks<P, R>()>(g, L, st);
+      return launch_q64<P, R, Q_MRHS, false>(g, L, st);
     case Q_BPLAIN:
       if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64) return launch_q5<P, R, Q_BPLAIN, true, 1, 256, 1>(g, L, st);

@@ -26,6 +26,8 @@ enum CgScalar {
   CG_BNORM2 = 11,     // ||b||^2
   CG_ASCALE = 12,     // A = ascale * Q^2
   CG_SIGMA0 = 13,     // base shift
+  CG_LIVE_SUM = 14,   // sum over iterations of the shifts whose direction p_l was updated
+  CG_ACTIVE_SUM = 15, // sum over iterations of the shifts whose solution (x_l or its y term) was updated
   CG_NSCALAR = 16
 };
 enum CgArray {
@@ -73,6 +75,8 @@ struct QLaunch {
   int nrhs;           // right-hand sides in one launch (0 or 1: one)
   int64_t rhs_stride; // bytes between consecutive RHS fields
   int64_t cgs_stride; // doubles between consecutive systems' scalar blocks (batched modes)
+  int krhs;           // Q_MRHS, FP32/FP16: right-hand sides per thread sharing each link (0 or 1: one,
+                      // q_kernel; 2 or 3: dslash_mrhs.cu)
 };
 int default_split(int prec, int recon, bool half);
 
@@ -82,6 +86,8 @@ cudaError_t launch_q(const Geom& g, const QLaunch& L, cudaStream_t st);
 // RHS run back to back and the links come from DRAM once (Q_PLAIN, no reduction, one warp per
 // site).
 cudaError_t launch_q_mrhs(const Geom& g, const QLaunch& L, int nrhs, size_t stride, cudaStream_t st);
+// Q_MRHS with L.krhs (2 or 3) right-hand sides per thread (FP32 / FP16; dslash_mrhs.cu).
+cudaError_t launch_q_mrhs_k(const Geom& g, const QLaunch& L, cudaStream_t st);
 
 // Several lattices in one persistent launch (dslash_batched.cu): lattice k applies Q to nrhs
 // fields at in + r * stride; its tiles (64 sites of one RHS) start at tile_begin in the list.
@@ -129,6 +135,11 @@ cudaError_t blas_axpby(const Geom& g, int prec, void* z, double a, const void* x
 cudaError_t blas_dot(const Geom& g, int prec, const void* x, const void* y, ReduceSlot slot, cudaStream_t st);
 // out (prec_out) = in (prec_in); out may not alias in unless the precisions match
 cudaError_t blas_convert(const Geom& g, int prec_out, void* out, int prec_in, const void* in, cudaStream_t st);
+// out (FP32 or FP16) = in (FP64) / sqrt(*norm2_dev) (device scalar; zero field when it is zero)
+cudaError_t blas_convert_normalized(const Geom& g, int prec_out, void* out, const void* in, const double* norm2_dev,
+                                    cudaStream_t st);
+// x64 (FP64) += a e32 (FP32)
+cudaError_t blas_axpy_widen(const Geom& g, void* x64, double a, const void* e32, cudaStream_t st);
 // out = gamma5 in (any precision; out may alias in)
 cudaError_t blas_g5(const Geom& g, int prec, void* out, const void* in, cudaStream_t st);
 // out = c1 x + c2 gamma5 y  (FP64 fields)

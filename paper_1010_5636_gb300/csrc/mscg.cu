@@ -40,6 +40,8 @@ __global__ void mscg_init_kernel(double* s, int n) {
     s[CG_ITER] = 0.0;
     s[CG_ALPHA_PREV] = 1.0;
     s[CG_BETA_PREV] = 0.0;
+    s[CG_LIVE_SUM] = 0.0;
+    s[CG_ACTIVE_SUM] = 0.0;
     s[CG_BNORM2] = s[CG_RR];
     s[CG_SIGMA0] = s[sh(SH_SIGMA, 0)];
     if (!(s[CG_RR] > 0.0)) {  // zero (or NaN) source: nothing to do
@@ -72,9 +74,11 @@ __global__ void mscg_scalar_kernel(double* s, int n, int maxit, cudaGraphConditi
   const double s0 = s[CG_SIGMA0];
   const double rnorm_rel = sqrt(rrn / s[CG_BNORM2]);
   int active_after = 0;
+  const bool active = l < n && s[sh(SH_ACTIVE, l)] != 0.0;
+  const bool live = l < n && (active || l == 0);
+  // work counters of this iteration's update kernel (read by the host for the byte count)
+  const int n_live = __syncthreads_count(live), n_active = __syncthreads_count(active);
   if (l < n) {
-    const bool active = s[sh(SH_ACTIVE, l)] != 0.0;
-    const bool live = active || l == 0;
     s[sh(SH_UPD, l)] = active ? 1.0 : 0.0;
     s[sh(SH_LIVE, l)] = live ? 1.0 : 0.0;
     if (live) {
@@ -99,6 +103,8 @@ __global__ void mscg_scalar_kernel(double* s, int n, int maxit, cudaGraphConditi
   if (l == 0) {
     const double it = s[CG_ITER] + 1.0;
     s[CG_ITER] = it;
+    s[CG_LIVE_SUM] += (double)n_live;
+    s[CG_ACTIVE_SUM] += (double)n_active;
     s[CG_ALPHA_PREV] = alpha;
     s[CG_BETA_PREV] = beta;
     s[CG_RR] = rrn;

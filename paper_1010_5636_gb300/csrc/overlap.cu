@@ -156,6 +156,9 @@ static nd_status sign_impl(nd_ctx* c, const double* in, const nd_dn_params* p, n
     if (s != ND_OK) return s;
     inf.iters = inf.sloppy_iters = ms.iters;
     for (int k = 0; k < n; ++k) inf.max_resid = std::max(inf.max_resid, ms.res[k]);
+    inf.krylov_ms = ms.ms;
+    inf.krylov_live_shifts = (int)ms.live;
+    inf.krylov_active_shifts = (int)ms.active;
   } else {
     MixedStats ms;
     ND_TRY_CUDA(c, cudaMemsetAsync(y, 0, fs, c->stream));
@@ -169,6 +172,12 @@ static nd_status sign_impl(nd_ctx* c, const double* in, const nd_dn_params* p, n
     inf.sloppy_iters = ms.sloppy_iters;
     inf.outer = ms.outer;
     inf.max_resid = ms.max_resid;
+    inf.krylov_ms = ms.krylov_ms;
+    inf.krylov_live_shifts = (int)ms.live;
+    inf.krylov_active_shifts = (int)ms.active;
+    inf.residuals64 = ms.residuals64;
+    inf.correction_iters = ms.correction_iters;
+    inf.refine_ms = ms.refine_ms;
   }
   // z = X y = Q y / sqrt(lambda_max); then z <- z - P z + sum_k sgn(nu_k) c_k u_k
   ND_TRY(q_apply(c, 0, z, y, 1.0 / std::sqrt(lam)));

@@ -175,10 +175,12 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
   double hs[CG_NSCALAR];
   if (!c->links[ps]) return fail(c, ND_ERR_STATE, "multi-shift CG: links not set in the Krylov precision");
   nd_ms_graph* G = ms_graph(c, ps, px, ymode, r, t, p_all, fs, x_or_y, fx, state, n, maxit);
+  ND_TRY_CUDA(c, cudaEventRecord(c->ev[0], c->stream));
   if (G) {
     // the whole solve is one graph launch: the iterations loop on the device until the scalar
     // kernel ends the while-loop
     ND_TRY_CUDA(c, cudaGraphLaunch(G->exec, c->stream));
+    ND_TRY_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
     ND_TRY(read_back(c, state, hs, CG_NSCALAR));
   } else {
     int chunk = 8;
@@ -190,6 +192,7 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
       if (hs[CG_DONE] != 0.0 || hs[CG_PENDING] != 0.0) break;
       chunk = std::min(chunk * 2, 64);
     }
+    ND_TRY_CUDA(c, cudaEventRecord(c->ev[1], c->stream));
   }
   std::vector<double> res(n);
   ND_TRY(read_back(c, state + sh(SH_RES, 0), res.data(), n));
@@ -197,6 +200,11 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
     out->iters = (int)hs[CG_ITER];
     out->status = (int)hs[CG_STATUS];
     out->res = res;
+    float ms = 0.f;
+    ND_TRY_CUDA(c, cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]));
+    out->ms = ms;
+    out->live = hs[CG_LIVE_SUM];
+    out->active = hs[CG_ACTIVE_SUM];
   }
   const int stt = (int)hs[CG_STATUS];
   if (stt != ND_OK) {
@@ -364,6 +372,15 @@ nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<d
   return ND_OK;
 }
 
+nd_status residual64_dev(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale,
+                         double* norm2_dev) {
+  void* t = field(c, "res_t", 0);
+  if (!t) return fail(c, ND_ERR_OOM, "residual: workspace");
+  ND_TRY(q_apply(c, 0, t, x));
+  ND_TRY(q_apply(c, 0, r, t, -ascale, -sigma, x, norm2_dev, nullptr, b, 1.0));
+  return ND_OK;
+}
+
 nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale, double bnorm2,
                      double* rel) {
   void* t = field(c, "res_t", 0);
@@ -423,13 +440,21 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   st->iters = ms.iters;
   st->sloppy_iters = ms.iters;
   st->max_resid = 0.0;
+  st->krylov_ms = ms.ms;
+  st->live = ms.live;
+  st->active = ms.active;
+  const auto t_refine = std::chrono::steady_clock::now();
   // FP64 defect correction of every shift, the correction solves of all shifts that still miss
-  // their target batched into one lockstep CG (one multi-RHS Q launch per step)
+  // their target batched into one lockstep CG (one multi-RHS Q launch per step).  A sweep computes
+  // the FP64 residuals of all open shifts back to back, each normalised into its FP32 correction
+  // source on the device, and reads their norms back once.
   const size_t f32 = (size_t)spinor_bytes(1, c->Vh), f64 = (size_t)spinor_bytes(0, c->Vh);
   char* X64 = static_cast<char*>(field(c, "mx_X64", 0, n));
   char* R32 = static_cast<char*>(field(c, "mx_R32", 1, n));
   char* E32 = static_cast<char*>(field(c, "mx_E32", 1, n));
-  if (!X64 || !R32 || !E32) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
+  // [2l, 2l + 1]: ||r_l||^2 and the residual launch's second norm; [2 CG_NMAX + l]: ||x_l||^2
+  double* nrm = static_cast<double*>(workspace(c, "mx_norms", sizeof(double) * 3 * CG_NMAX));
+  if (!X64 || !R32 || !E32 || !nrm) return fail(c, ND_ERR_OOM, "mixed solve: workspace");
   for (int l = 0; l < n; ++l) {
     ND_TRY_CUDA(c, blas_convert(c->g, 0, X64 + l * f64, 1, x32 + l * f32, c->stream));
     ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, bnorm, X64 + l * f64, 0.0, nullptr, false, slot(c, nullptr),
@@ -439,22 +464,36 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   // per-shift reduction asked of a correction solve; raised tenfold (up to 1e-2) after a correction
   // that ran into its iteration cap: an FP32 CG resolves relative reductions down to about
   // u_32 kappa, which the lowest shifts of a deflated system only just clear
-  std::vector<double> tin(n, floor_in), rnorm(n, 1.0);
+  std::vector<double> tin(n, floor_in), rnorm(n, 1.0), h(3 * CG_NMAX, 0.0);
   std::vector<int> outer(n, 0), flat(n, 0);
   std::vector<bool> done(n, false);
+  // a correction asks for a modest reduction; needing many more iterations than the sloppy pass
+  // means it is stuck on rounding, and the next FP64 residual decides (rounded up to a power of two:
+  // the captured graph is keyed by the limit)
+  int cap = 128;
+  while (cap < 8 * st->iters + 100) cap *= 2;
   for (int sweep = 0;; ++sweep) {
-    std::vector<int> pend;
-    std::vector<double> sig_p, tol_p;
+    auto tr = now();
     for (int l = 0; l < n; ++l) {
       if (done[l]) continue;
-      auto tr = now();
-      ND_TRY(residual64(c, r64, b64, X64 + l * f64, sigma[l], ascale, bnorm2, &rel[l]));
-      if (trace) t_res += ms_since(tr);
-      if (first[l] < 0) first[l] = rel[l];
-      if (rel[l] <= tol[l]) {
-        done[l] = true;
-        continue;
+      // r = b - (ascale Q^2 + sigma_l) x_l in FP64, ||r||^2 -> nrm[l]; R32_l = r / ||r||
+      ND_TRY(residual64_dev(c, r64, b64, X64 + l * f64, sigma[l], ascale, nrm + 2 * l));
+      ND_TRY_CUDA(c, blas_convert_normalized(c->g, 1, R32 + l * f32, r64, nrm + 2 * l, c->stream));
+      if (flat[l] >= 1) {  // ||x_l||^2 for the rounding-floor test below (r64 is free again)
+        ND_TRY_CUDA(c, blas_axpby(c->g, 0, r64, 1.0, X64 + l * f64, 0.0, nullptr, true,
+                                  slot(c, nrm + 2 * CG_NMAX + l), c->stream));
       }
+      ++st->residuals64;
+    }
+    ND_TRY(read_back(c, nrm, h.data(), 3 * CG_NMAX));
+    if (trace) t_res += ms_since(tr);
+    std::vector<double> sig_p(n), tol_p(n, 1.0);
+    int npend = 0;
+    for (int l = 0; l < n; ++l) {
+      sig_p[l] = sigma[l];
+      if (done[l]) continue;
+      rel[l] = std::sqrt(h[2 * l] / bnorm2);
+      if (first[l] < 0) first[l] = rel[l];
       // A correction that no longer halves the FP64 residual twice in a row means the target lies
       // at or below what an FP64 residual of this system resolves: |fl(b - A x) - (b - A x)| is
       // about u (||b|| + || |A| || ||x||) with ||A|| <= ascale lambda_max + sigma ~ 1 + sigma; the
@@ -463,55 +502,51 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
       // residual reported; above it the solve fails.
       flat[l] = rel[l] > 0.5 * prev[l] ? flat[l] + 1 : 0;
       prev[l] = rel[l];
-      if (flat[l] >= 2) {
-        double xn2;
-        ND_TRY_CUDA(c, blas_axpby(c->g, 0, r64, 1.0, X64 + l * f64, 0.0, nullptr, true, slot(c, c->red_scratch + 12),
-                                  c->stream));
-        ND_TRY(read_back(c, c->red_scratch + 12, &xn2, 1));
+      if (rel[l] <= tol[l]) {
+        done[l] = true;
+      } else if (flat[l] >= 2) {
+        // flat[l] >= 2 means it was >= 1 before this sweep, so ||x_l||^2 was reduced above
+        const double xn2 = h[2 * CG_NMAX + l];
         const double floor64 = 256.0 * 1.1102230246251565e-16 * (1.0 + (1.0 + sigma[l]) * std::sqrt(xn2 / bnorm2));
-        if (rel[l] <= floor64) {
-          done[l] = true;
-          continue;
+        if (rel[l] > floor64) {
+          char msg[160];
+          std::snprintf(msg, sizeof msg, "mixed solve: shift %d stagnates at relative residual %.3g (target %.3g)",
+                        l, rel[l], tol[l]);
+          return fail(c, ND_ERR_NOT_CONVERGED, msg);
         }
-        char msg[160];
-        std::snprintf(msg, sizeof msg, "mixed solve: shift %d stagnates at relative residual %.3g (target %.3g)", l,
-                      rel[l], tol[l]);
-        return fail(c, ND_ERR_NOT_CONVERGED, msg);
+        done[l] = true;
+      } else {
+        rnorm[l] = rel[l] * bnorm;
+        tol_p[l] = std::max(0.3 * tol[l] / rel[l], tin[l]);
+        ++npend;
       }
-      // r64 / ||r64|| to FP32 (see above); the correction is scaled back by rnorm[l]
-      rnorm[l] = rel[l] * bnorm;
-      ND_TRY_CUDA(c, blas_axpby(c->g, 0, r64, 1.0 / rnorm[l], r64, 0.0, nullptr, false, slot(c, nullptr), c->stream));
-      ND_TRY_CUDA(c, blas_convert(c->g, 1, R32 + pend.size() * f32, 0, r64, c->stream));
-      pend.push_back(l);
-      sig_p.push_back(sigma[l]);
-      tol_p.push_back(std::max(0.3 * tol[l] / rel[l], tin[l]));
+      // a shift that is done takes part in the batched solve with a zero source (it stops at once)
+      if (done[l]) ND_TRY_CUDA(c, cudaMemsetAsync(R32 + l * f32, 0, f32, c->stream));
     }
-    if (pend.empty()) break;
+    if (npend == 0) {
+      st->refine_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_refine).count();
+      break;
+    }
     if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
     std::vector<int> it;
     auto tb = now();
-    // a correction asks for a modest reduction; needing many more iterations than the sloppy pass
-    // means it is stuck on rounding, and the next FP64 residual decides
-    // (rounded up to a power of two: the captured graph is keyed by the limit)
-    int cap = 128;
-    while (cap < 8 * st->iters + 100) cap *= 2;
     s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, std::min(maxit, cap), &it);
     if (s != ND_OK) return s;
     if (trace) {
       const double dt = ms_since(tb);
       t_bcg += dt;
-      std::fprintf(stderr, "mixed solve: sweep %d, %zu systems, batched CG max %d iterations %.2f ms\n", sweep,
-                   pend.size(), *std::max_element(it.begin(), it.end()), dt);
+      std::fprintf(stderr, "mixed solve: sweep %d, %d systems, batched CG max %d iterations %.2f ms\n", sweep, npend,
+                   *std::max_element(it.begin(), it.end()), dt);
     }
     auto tu = now();
-    for (size_t k = 0; k < pend.size(); ++k) {
-      const int l = pend[k];
-      st->sloppy_iters += it[k];
-      if (it[k] >= std::min(maxit, cap)) tin[l] = std::min(10.0 * tin[l], 1e-2);
+    for (int l = 0; l < n; ++l) {
+      if (done[l]) continue;
+      st->sloppy_iters += it[l];
+      st->correction_iters += it[l];
+      if (it[l] >= std::min(maxit, cap)) tin[l] = std::min(10.0 * tin[l], 1e-2);
       ++outer[l];
-      ND_TRY_CUDA(c, blas_convert(c->g, 0, r64, 1, E32 + k * f32, c->stream));
-      ND_TRY_CUDA(c, blas_axpby(c->g, 0, X64 + l * f64, 1.0, X64 + l * f64, rnorm[l], r64, false, slot(c, nullptr),
-                                c->stream));
+      // x_l += ||r_l|| e_l in FP64
+      ND_TRY_CUDA(c, blas_axpy_widen(c->g, X64 + l * f64, rnorm[l], E32 + l * f32, c->stream));
     }
     if (trace) t_upd += ms_since(tu);
   }

@@ -22,6 +22,9 @@ struct MsResult {
   int iters = 0;
   int status = ND_OK;
   std::vector<double> res;  // per-shift recurrence residual (relative to ||b||)
+  double ms = 0.0;          // device time of the iterations (CUDA events on the context's stream)
+  double live = 0.0;        // sum over iterations of the shifts whose p_l was updated
+  double active = 0.0;      // sum over iterations of the shifts whose x_l (or y term) was updated
 };
 
 // Multi-shift CG on A = ascale * Q^2 with shifts sigma[0..n) (ascending, sigma[0] the base).
@@ -31,6 +34,9 @@ nd_status mscg_run(nd_ctx* c, int ps, int px, bool ymode, const void* b, void* x
                    const std::vector<double>& tol, const std::vector<double>& w, double ascale, int maxit,
                    MsResult* out);
 
+// r = b - (ascale Q^2 + sigma) x in FP64, ||r||^2 reduced into norm2_dev (device), no host sync.
+nd_status residual64_dev(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale,
+                         double* norm2_dev);
 // r = b - (ascale Q^2 + sigma) x in FP64; returns ||r|| / ||b|| through *rel (bnorm2 given).
 nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double sigma, double ascale, double bnorm2,
                      double* rel);
@@ -41,6 +47,10 @@ nd_status residual64(nd_ctx* c, void* r, const void* b, const void* x, double si
 struct MixedStats {
   int iters = 0, sloppy_iters = 0, outer = 0;
   double max_resid = 0.0;
+  double krylov_ms = 0.0, live = 0.0, active = 0.0;  // the sloppy multi-shift pass (MsResult)
+  int residuals64 = 0;                                // FP64 residuals of the refinement
+  int correction_iters = 0;                           // correction-solve iterations summed over systems
+  double refine_ms = 0.0;                             // wall time of the refinement
 };
 template <typename Sink>
 nd_status mixed_solve(nd_ctx* c, int ps, const void* b64, double bnorm2, const std::vector<double>& sigma,

@@ -5,8 +5,8 @@
 // same every time, and out never aliases in for these launches); the fastest median batch wins.
 // Batches measure the steady state the solvers see: one launch timed alone between host
 // synchronisations favoured shapes that are not faster in a stream of launches.  Choices live in memory for the process and, if
-// ND_AUTOTUNE_CACHE names a file, are read from and appended to it (one "key split threads"
-// line each).  ND_AUTOTUNE=0 turns tuning off (defaults: one warp per site, 64 threads).
+// ND_AUTOTUNE_CACHE names a file, are read from and appended to it (one "key split threads krhs"
+// line each).  Multi-RHS launches also try 2 and 3 right-hand sides per thread.  ND_AUTOTUNE=0 turns tuning off (defaults: one warp per site, 64 threads).
 #include <algorithm>
 #include <cstdio>
 #include <cstdlib>
@@ -21,7 +21,10 @@ namespace nd {
 
 namespace {
 std::mutex g_tune_mutex;
-std::map<std::string, std::pair<int, int>> g_tuned;
+struct Shape {
+  int split, threads, krhs;
+};
+std::map<std::string, Shape> g_tuned;
 bool g_loaded = false;
 
 std::string tune_key(const Geom& g, const QLaunch& L) {
@@ -39,17 +42,17 @@ void load_cache() {
   FILE* f = std::fopen(path, "r");
   if (!f) return;
   char key[160];
-  int split, threads;
-  while (std::fscanf(f, "%159s %d %d", key, &split, &threads) == 3) g_tuned[key] = {split, threads};
+  int split, threads, krhs;
+  while (std::fscanf(f, "%159s %d %d %d", key, &split, &threads, &krhs) == 4) g_tuned[key] = {split, threads, krhs};
   std::fclose(f);
 }
 
-void store_cache(const std::string& key, int split, int threads) {
+void store_cache(const std::string& key, const Shape& c) {
   const char* path = std::getenv("ND_AUTOTUNE_CACHE");
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d\n", key.c_str(), split, threads);
+  std::fprintf(f, "%s %d %d %d\n", key.c_str(), c.split, c.threads, c.krhs);
   std::fclose(f);
 }
 }  // namespace
@@ -69,24 +72,30 @@ cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st) {
     load_cache();
     auto it = g_tuned.find(key);
     if (it != g_tuned.end()) {
-      L.split = it->second.first;
-      L.threads = it->second.second;
+      L.split = it->second.split;
+      L.threads = it->second.threads;
+      L.krhs = it->second.krhs;
       return cudaSuccess;
     }
   }
-  std::vector<std::pair<int, int>> cand = {{1, 0}, {1, 256}};
+  std::vector<Shape> cand = {{1, 0, 1}, {1, 256, 1}};
   if (L.mode == Q_PLAIN && L.prec != 0) {
-    cand.push_back({2, 0});
-    cand.push_back({4, 0});
+    cand.push_back({2, 0, 1});
+    cand.push_back({4, 0, 1});
+  }
+  if (L.mode == Q_MRHS && L.prec != 0 && L.nrhs > 1) {
+    cand.push_back({1, 0, 2});
+    if (L.nrhs > 2) cand.push_back({1, 0, 3});
   }
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaGetLastError();
   float best = 1e30f;
-  std::pair<int, int> pick = cand[0];
+  Shape pick = cand[0];
   for (const auto& c : cand) {
     QLaunch T = L;
-    T.split = c.first;
-    T.threads = c.second;
+    T.split = c.split;
+    T.threads = c.threads;
+    T.krhs = c.krhs;
     std::vector<float> ts;
     for (int w = 0; w < 2; ++w) {
       cudaError_t e = launch_q(g, T, st);
@@ -122,11 +131,12 @@ cudaError_t autotune_launch(const Geom& g, QLaunch& L, cudaStream_t st) {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     if (!g_tuned.count(key)) {
       g_tuned[key] = pick;
-      store_cache(key, pick.first, pick.second);
+      store_cache(key, pick);
     }
   }
-  L.split = pick.first;
-  L.threads = pick.second;
+  L.split = pick.split;
+  L.threads = pick.threads;
+  L.krhs = pick.krhs;
   return cudaSuccess;
 }
 

@@ -310,3 +310,49 @@ def test_autotune_cache_file(nd, tmp_path):
     assert len([ln for ln in lines if ln.startswith("q:")]) == 2
     subprocess.run([sys.executable, "-c", code], check=True, env=env, cwd=os.getcwd())
     assert len([ln for ln in cache.read_text().split("\n") if ln.startswith("q:")]) == 2  # reused, not retuned
+
+
+@pytest.mark.parametrize("krhs", [2, 3])
+def test_Q_multi_rhs_per_thread(krhs):
+    """Several RHS per thread sharing each link (ND_Q_KRHS, read once per process, hence a child
+    process): FP32 and FP16 results equal single applications to the storage precision's rounding
+    (the two kernels may contract the epilogue into fused multiply-adds differently) and match the
+    oracle."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, %r)
+import synth, paper_1010_5636_gb300 as nd
+from oracle import wilson
+from tests.gpu_util import dev, host, rel
+dims = (4, 6, 4, 8)
+V = int(np.prod(dims))
+U = synth.gauge_field(dims, "haar", seed=0)
+for prec, recon, tol in ((1, 12, 1e-5), (1, 18, 1e-5), (2, 12, 2e-3)):
+    for nrhs in (2, 5, 7):
+        psi = synth.spinor(dims, seed=3, nrhs=nrhs)
+        ctx = nd.nd_create(dims, m=-1.4)
+        rc = [0, 0, 0]; rc[prec] = recon
+        nd.nd_set_links(ctx, dev(U), rc)
+        sb = nd.nd_spinor_bytes(ctx, prec)
+        a = torch.empty(sb * nrhs, dtype=torch.uint8, device="cuda")
+        nd.nd_pack_spinor(ctx, a, dev(psi), prec, nrhs)
+        b = torch.empty_like(a); one = torch.empty_like(a)
+        nd.nd_apply_Q(ctx, b, a, prec, nrhs)
+        for r in range(nrhs):
+            nd.nd_apply_Q(ctx, one[r * sb:(r + 1) * sb], a[r * sb:(r + 1) * sb], prec, 1)
+        got = torch.empty((nrhs, V, 4, 3), dtype=torch.complex128, device="cuda")
+        ref = torch.empty_like(got)
+        nd.nd_unpack_spinor(ctx, got, b, prec, nrhs)
+        nd.nd_unpack_spinor(ctx, ref, one, prec, nrhs)
+        torch.cuda.synchronize()
+        assert rel(host(got), host(ref)) <= (1e-6 if prec == 1 else 1e-3), (prec, recon, nrhs)
+        assert rel(host(got), wilson.apply_Q(U, psi, dims, -1.4)) <= tol
+        nd.nd_destroy(ctx)
+print("ok")
+''' % os.getcwd()
+    env = dict(os.environ, ND_Q_KRHS=str(krhs), ND_AUTOTUNE="0")
+    r = subprocess.run([sys.executable, "-c", code], env=env, cwd=os.getcwd(), capture_output=True, text=True)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-2000:]
