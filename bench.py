@@ -622,16 +622,18 @@ def clenshaw_phase(nd, torch, degree=200, reps=3):
 def profile_case(nd, torch, case):
     """Small cases for ncu captures (a few launches, a few hundred MB on the device)."""
     import synth
-    if case == "hop24":
+    if case in ("hop24", "hop24_fp16"):
+        # three one-parity hopping launches on 24^3x48 (FP32 or FP16 storage, 12-real links)
+        prec = 1 if case == "hop24" else 2
         dims = (48, 24, 24, 24)
         U = torch.from_numpy(synth.gauge_field(dims, "near_identity", seed=0, eps=0.3)).cuda()
         ctx = nd.nd_create(dims, m=-1.4, s=0.4)
-        nd.nd_set_links(ctx, U, (0, RECON, 0))
-        a = torch.empty(nd.nd_spinor_bytes(ctx, 1), dtype=torch.uint8, device="cuda")
+        nd.nd_set_links(ctx, U, (0, RECON if prec == 1 else 0, RECON if prec == 2 else 0))
+        a = torch.empty(nd.nd_spinor_bytes(ctx, prec), dtype=torch.uint8, device="cuda")
         b = torch.empty_like(a)
-        nd.nd_pack_spinor(ctx, a, torch.from_numpy(synth.spinor(dims, seed=1)).cuda(), 1)
+        nd.nd_pack_spinor(ctx, a, torch.from_numpy(synth.spinor(dims, seed=1)).cuda(), prec)
         for _ in range(3):
-            nd.nd_apply_Q_parity(ctx, b, a, 1, 0, 0.0)
+            nd.nd_apply_Q_parity(ctx, b, a, prec, 0, 0.0)
         torch.cuda.synchronize()
         nd.nd_destroy(ctx)
     elif case == "clen24":
@@ -846,7 +848,7 @@ def main():
                     help="skip the D_N comparison with the FP64 oracle (about a minute of host time)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None,
-                    help="run a small profiling case and exit (hop24, clen24, dn16, dn16_fp64, dn16_fp16)")
+                    help="run a small profiling case and exit (hop24, hop24_fp16, clen24, dn16, dn16_fp64, dn16_fp16)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

@@ -112,6 +112,7 @@ nd_status nd_create(nd_ctx** out, const int dims[4], int antiperiodic_t, double 
   g.Vh = (int)c->Vh;
   g.apbc = antiperiodic_t ? 1 : 0;
   g.even_only = 0;
+  geom_set_divisors(g);
   // ND_GRAPHS=0: run the Krylov iterations as host-issued launches instead of captured graphs (a
   // profiler cannot see the kernel nodes of a graph with a conditional while-loop)
   if (const char* e = std::getenv("ND_GRAPHS")) c->graphs_ok = std::atoi(e) != 0;

@@ -104,23 +104,151 @@ __device__ __forceinline__ void hop(Spinor<typename Traits<P>::real>& acc, const
   spin_accumulate<MU, FWD>(acc, c);
 }
 
+// ------------------------------------------------------------------ packed FP32 form
+// FP32 and FP16 storage run the hop on spin-row pairs (Spinor2): both rows of a half spinor meet
+// the same link entries, so every SU(3) multiply-add, projection sum and accumulation acts on a
+// pair (s0, s1) or (s2, s3) with one f32x2 instruction.  Per lane the operations and their order
+// are those of the scalar hop above.
+
+__device__ __forceinline__ float2 f2_swap(float2 a) { return make_float2(a.y, a.x); }
+__device__ __forceinline__ float2 f2_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_bcast(float a) { return make_float2(a, a); }
+
+// Half spinor pairs hr[i] = (h0[i].re, h1[i].re), hi[i] = (h0[i].im, h1[i].im) of spin_project.
+template <int MU, bool FWD>
+__device__ __forceinline__ void spin_project2(const Spinor2& s, float2 (&hr)[3], float2 (&hi)[3]) {
+  const float2 pm = make_float2(1.f, -1.f), mp = make_float2(-1.f, 1.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if constexpr (MU == 0) {  // h0 = s0 -+ (-s2), h1 = s1 -+ (-s3)
+      hr[i] = FWD ? f2_add(s.ur[i], s.dr[i]) : f2_add(s.ur[i], f2_neg(s.dr[i]));
+      hi[i] = FWD ? f2_add(s.ui[i], s.di[i]) : f2_add(s.ui[i], f2_neg(s.di[i]));
+    } else if constexpr (MU == 1) {  // h0 = s0 +- i s3, h1 = s1 +- i s2
+      hr[i] = FWD ? f2_add(s.ur[i], f2_neg(f2_swap(s.di[i]))) : f2_add(s.ur[i], f2_swap(s.di[i]));
+      hi[i] = FWD ? f2_add(s.ui[i], f2_swap(s.dr[i])) : f2_add(s.ui[i], f2_neg(f2_swap(s.dr[i])));
+    } else if constexpr (MU == 2) {  // h0 = s0 +- s3, h1 = s1 -+ s2
+      hr[i] = f2_fma(f2_swap(s.dr[i]), FWD ? pm : mp, s.ur[i]);
+      hi[i] = f2_fma(f2_swap(s.di[i]), FWD ? pm : mp, s.ui[i]);
+    } else {  // h0 = s0 +- i s2, h1 = s1 -+ i s3
+      hr[i] = f2_fma(s.di[i], FWD ? mp : pm, s.ur[i]);
+      hi[i] = f2_fma(s.dr[i], FWD ? pm : mp, s.ui[i]);
+    }
+  }
+}
+
+// c = U h (forward) or U^dagger h (backward) on the pairs: c_re += u_re h_re - u_im h_im,
+// c_im += u_re h_im + u_im h_re (conj(u) for the dagger), in the order of cfma / cfmac.
+template <bool DAG>
+__device__ __forceinline__ void colour_mul2(const Su3<float>& U, const float2 (&hr)[3], const float2 (&hi)[3],
+                                            float2 (&cr)[3], float2 (&ci)[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float2 vr = make_float2(0.f, 0.f), vi = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cx<float> u = DAG ? U.e[j][i] : U.e[i][j];
+      const float2 ur = f2_bcast(u.re), ui = f2_bcast(u.im), un = f2_bcast(-u.im);
+      vr = f2_fma(ur, hr[j], vr);
+      vr = f2_fma(DAG ? ui : un, hi[j], vr);
+      vi = f2_fma(ur, hi[j], vi);
+      vi = f2_fma(DAG ? un : ui, hr[j], vi);
+    }
+    cr[i] = vr;
+    ci[i] = vi;
+  }
+}
+
+// acc += [c ; S B^dagger c] (spin_accumulate on the pairs).
+template <int MU, bool FWD>
+__device__ __forceinline__ void spin_accumulate2(Spinor2& acc, const float2 (&cr)[3], const float2 (&ci)[3]) {
+  const float2 pm = make_float2(1.f, -1.f), mp = make_float2(-1.f, 1.f);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    acc.ur[i] = f2_add(acc.ur[i], cr[i]);
+    acc.ui[i] = f2_add(acc.ui[i], ci[i]);
+    if constexpr (MU == 0) {  // fwd (+c0, +c1), bwd (-c0, -c1)
+      acc.dr[i] = FWD ? f2_add(acc.dr[i], cr[i]) : f2_add(acc.dr[i], f2_neg(cr[i]));
+      acc.di[i] = FWD ? f2_add(acc.di[i], ci[i]) : f2_add(acc.di[i], f2_neg(ci[i]));
+    } else if constexpr (MU == 1) {  // fwd (-i c1, -i c0), bwd (+i c1, +i c0)
+      acc.dr[i] = FWD ? f2_add(acc.dr[i], f2_swap(ci[i])) : f2_add(acc.dr[i], f2_neg(f2_swap(ci[i])));
+      acc.di[i] = FWD ? f2_add(acc.di[i], f2_neg(f2_swap(cr[i]))) : f2_add(acc.di[i], f2_swap(cr[i]));
+    } else if constexpr (MU == 2) {  // fwd (-c1, +c0), bwd (+c1, -c0)
+      acc.dr[i] = f2_fma(f2_swap(cr[i]), FWD ? mp : pm, acc.dr[i]);
+      acc.di[i] = f2_fma(f2_swap(ci[i]), FWD ? mp : pm, acc.di[i]);
+    } else {  // fwd (-i c0, +i c1), bwd (+i c0, -i c1)
+      acc.dr[i] = f2_fma(ci[i], FWD ? pm : mp, acc.dr[i]);
+      acc.di[i] = f2_fma(cr[i], FWD ? mp : pm, acc.di[i]);
+    }
+  }
+}
+
+// One hop of the FP32 / FP16 operator on spin-row pairs.
+template <int P, int R, int MU, bool FWD>
+__device__ __forceinline__ void hop2(Spinor2& acc, const Geom& g, const Site& s, int p, int h, const char* links,
+                                     const void* in) {
+  static_assert(P != P64, "the packed hop serves the FP32 arithmetic of FP32 and FP16 storage");
+  bool crossed;
+  const int hn = neighbour_h<MU, FWD>(g, s, &crossed);
+  Spinor2 nb;
+  SpinorIO<P>::load2(nb, in, g.Vh, 1 - p, hn);
+  LinkRaw<P, R> raw;
+  if (FWD)
+    load_raw<P, R>(raw, links, g.Vh, p, MU, h);
+  else
+    load_raw<P, R>(raw, links, g.Vh, 1 - p, MU, hn);
+  float2 hr[3], hi[3], cr[3], ci[3];
+  spin_project2<MU, FWD>(nb, hr, hi);
+  if (g.apbc && crossed) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      hr[i] = f2_neg(hr[i]);
+      hi[i] = f2_neg(hi[i]);
+    }
+  }
+  Su3<float> U;
+  reconstruct<P, R>(U, raw);
+  colour_mul2<!FWD>(U, hr, hi, cr, ci);
+  spin_accumulate2<MU, FWD>(acc, cr, ci);
+}
+
+__device__ __forceinline__ void zero2(Spinor2& a) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) a.ur[i] = a.ui[i] = a.dr[i] = a.di[i] = make_float2(0.f, 0.f);
+}
+
 // Sum of the eight hops: acc = sum_mu [U_mu(x)(1-gamma_mu)psi(x+mu) + U_mu(x-mu)^dag (1+gamma_mu) psi(x-mu)].
 template <int P, int R>
 __device__ __forceinline__ void hopping_sum(Spinor<typename Traits<P>::real>& acc, const Geom& g, const Site& s,
                                             int p, int h, const char* links, const void* in) {
   using T = typename Traits<P>::real;
+  if constexpr (P == P64) {
 #pragma unroll
-  for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int i = 0; i < 3; ++i) acc.s[a][i] = mk((T)0, (T)0);
-  hop<P, R, 0, true>(acc, g, s, p, h, links, in);
-  hop<P, R, 0, false>(acc, g, s, p, h, links, in);
-  hop<P, R, 1, true>(acc, g, s, p, h, links, in);
-  hop<P, R, 1, false>(acc, g, s, p, h, links, in);
-  hop<P, R, 2, true>(acc, g, s, p, h, links, in);
-  hop<P, R, 2, false>(acc, g, s, p, h, links, in);
-  hop<P, R, 3, true>(acc, g, s, p, h, links, in);
-  hop<P, R, 3, false>(acc, g, s, p, h, links, in);
+      for (int i = 0; i < 3; ++i) acc.s[a][i] = mk((T)0, (T)0);
+    hop<P, R, 0, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 0, false>(acc, g, s, p, h, links, in);
+    hop<P, R, 1, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 1, false>(acc, g, s, p, h, links, in);
+    hop<P, R, 2, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 2, false>(acc, g, s, p, h, links, in);
+    hop<P, R, 3, true>(acc, g, s, p, h, links, in);
+    hop<P, R, 3, false>(acc, g, s, p, h, links, in);
+  } else {
+    Spinor2 a2;
+    zero2(a2);
+    hop2<P, R, 0, true>(a2, g, s, p, h, links, in);
+    hop2<P, R, 0, false>(a2, g, s, p, h, links, in);
+    hop2<P, R, 1, true>(a2, g, s, p, h, links, in);
+    hop2<P, R, 1, false>(a2, g, s, p, h, links, in);
+    hop2<P, R, 2, true>(a2, g, s, p, h, links, in);
+    hop2<P, R, 2, false>(a2, g, s, p, h, links, in);
+    hop2<P, R, 3, true>(a2, g, s, p, h, links, in);
+    hop2<P, R, 3, false>(a2, g, s, p, h, links, in);
+    unpair(acc, a2);
+  }
 }
 
 }  // namespace nd

@@ -10,6 +10,7 @@
 // Epilogue: gamma5 and the diagonal (4+m) fused; optional y-term, fused FP64 norms, and the
 // fused CG residual update of the multi-shift solver.
 #pragma once
+#include <algorithm>
 #include "dslash.cuh"
 #include "kernels.h"
 #include "reduce.cuh"
@@ -22,6 +23,10 @@ template <int P, int R, int SPLIT>
 __device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& acc, const Geom& g, const Site& s,
                                              int p, int h, const char* links, const void* in, int part) {
   using T = typename Traits<P>::real;
+  if constexpr (SPLIT == 1) {
+    hopping_sum<P, R>(acc, g, s, p, h, links, in);
+    return;
+  }
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -44,8 +49,10 @@ __device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& a
   }
 }
 
-template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS = Q_THREADS, int MINB = 1>
-__global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A0) {
+// One block's share of a launch: the SITES output sites of block index blk of nblk (for the
+// multi-RHS and batched modes, blk runs over RHS fastest, then site blocks).
+template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS>
+__device__ __forceinline__ void q_block(const Geom& g, const QLaunch& A0, int blk, int nblk) {
   using T = typename Traits<P>::real;
   // batched modes run one independent system per RHS; BASE is the per-system operation
   constexpr bool BATCH = MODE == Q_BPLAIN || MODE == Q_BCG;
@@ -54,7 +61,6 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int part = SPLIT == 1 ? 0 : warp % SPLIT;
   const int jloc = (warp / SPLIT) * 32 + lane;
-  int blk = blockIdx.x, nblk = gridDim.x;
   QLaunch A = A0;
   ReduceSlot slot = A0.slot;
   if constexpr (MODE == Q_MRHS || BATCH) {
@@ -191,16 +197,43 @@ __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QL
   if (REDUCE) grid_sum<2>(red, slot, nblk, blk);
 }
 
+template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS = Q_THREADS, int MINB = 1>
+__global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A0) {
+  if constexpr (MODE == Q_BPLAIN || MODE == Q_BCG) {
+    // batched systems: a grid of resident blocks strides over the (system, site block) items, so
+    // the items of systems that have stopped cost one flag read each instead of a block launch
+    constexpr int SITES = THREADS / SPLIT;
+    const int items = (A0.nsites + SITES - 1) / SITES * A0.nrhs;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) q_block<P, R, MODE, REDUCE, SPLIT, THREADS>(g, A0, item, items);
+  } else {
+    q_block<P, R, MODE, REDUCE, SPLIT, THREADS>(g, A0, blockIdx.x, gridDim.x);
+  }
+}
+
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS, int MINB>
 static cudaError_t launch_q5(const Geom& g, const QLaunch& L, cudaStream_t st) {
   constexpr int SITES = THREADS / SPLIT;
-  const int blocks = (L.nsites + SITES - 1) / SITES * (L.nrhs > 1 ? L.nrhs : 1);
+  int blocks = (L.nsites + SITES - 1) / SITES * (L.nrhs > 1 ? L.nrhs : 1);
   const size_t smem = SPLIT > 1 ? (size_t)SPLIT * 24 * SITES * sizeof(typename Traits<P>::real) : 0;
   static bool attr = false;
   if (smem > 48 * 1024 && !attr) {
     cudaFuncSetAttribute(q_kernel<P, R, MODE, REDUCE, SPLIT, THREADS, MINB>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
+  }
+  if constexpr (MODE == Q_BPLAIN || MODE == Q_BCG) {
+    // one wave of resident blocks (per device, looked up once)
+    static int resident[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && resident[dev] == 0) {
+      int per_sm = 0, sms = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, q_kernel<P, R, MODE, REDUCE, SPLIT, THREADS, MINB>,
+                                                    THREADS, smem);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      resident[dev] = std::max(1, per_sm) * std::max(1, sms);
+    }
+    if (dev < 64) blocks = std::min(blocks, resident[dev]);
   }
   q_kernel<P, R, MODE, REDUCE, SPLIT, THREADS, MINB><<<blocks, THREADS, smem, st>>>(g, L);
   return cudaGetLastError();

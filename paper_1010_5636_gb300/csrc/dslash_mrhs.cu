@@ -3,7 +3,7 @@
 // the SU(3) reconstruction are shared by K right-hand sides, and each thread has K independent
 // neighbour loads in flight per hop.  Blocks with consecutive indices take the same 64 sites for
 // successive groups of K right-hand sides, so a tile of links also serves the other groups from L2.
-// The per-RHS arithmetic is the one of q_kernel, term for term in the same order.
+// The per-RHS arithmetic is the one of q_kernel (packed spin-row pairs), term for term in the same order.
 #include "dslash.cuh"
 #include "kernels.h"
 
@@ -13,35 +13,35 @@ constexpr int MR_THREADS = 64;
 constexpr int MR_MIN_BLOCKS = 6;
 
 template <int P, int R, int MU, bool FWD, int K>
-__device__ __forceinline__ void hop_k(Spinor<typename Traits<P>::real> (&acc)[K], const Geom& g, const Site& s, int p,
-                                      int h, const char* links, const char* in, int64_t stride, int kk) {
-  using T = typename Traits<P>::real;
+__device__ __forceinline__ void hop_k(Spinor2 (&acc)[K], const Geom& g, const Site& s, int p, int h,
+                                      const char* links, const char* in, int64_t stride, int kk) {
   bool crossed;
   const int hn = neighbour_h<MU, FWD>(g, s, &crossed);
-  Spinor<T> nb[K];
+  Spinor2 nb[K];
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (k < kk) SpinorIO<P>::load(nb[k], in + k * stride, g.Vh, 1 - p, hn);
+    if (k < kk) SpinorIO<P>::load2(nb[k], in + k * stride, g.Vh, 1 - p, hn);
   LinkRaw<P, R> raw;
   if (FWD)
     load_raw<P, R>(raw, links, g.Vh, p, MU, h);
   else
     load_raw<P, R>(raw, links, g.Vh, 1 - p, MU, hn);
-  Su3<T> U;
+  Su3<float> U;
   reconstruct<P, R>(U, raw);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (k >= kk) continue;
-    cx<T> hs[2][3], c[2][3];
-    spin_project<MU, FWD>(nb[k], hs);
+    float2 hr[3], hi[3], cr[3], ci[3];
+    spin_project2<MU, FWD>(nb[k], hr, hi);
     if (g.apbc && crossed) {
 #pragma unroll
-      for (int a = 0; a < 2; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) hs[a][i] = -hs[a][i];
+      for (int i = 0; i < 3; ++i) {
+        hr[i] = f2_neg(hr[i]);
+        hi[i] = f2_neg(hi[i]);
+      }
     }
-    colour_mul<!FWD>(U, hs, c);
-    spin_accumulate<MU, FWD>(acc[k], c);
+    colour_mul2<!FWD>(U, hr, hi, cr, ci);
+    spin_accumulate2<MU, FWD>(acc[k], cr, ci);
   }
 }
 
@@ -69,33 +69,30 @@ __global__ void __launch_bounds__(MR_THREADS, MR_MIN_BLOCKS)
   const Site s = site_of(g, p, h);
   const char* in0 = in + r0 * stride;
   char* out0 = out + r0 * stride;
-  Spinor<T> acc[K];
+  Spinor2 acc2[K];
 #pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) acc[k].s[a][c] = mk((T)0, (T)0);
-  hop_k<P, R, 0, true, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 0, false, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 1, true, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 1, false, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 2, true, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 2, false, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 3, true, K>(acc, g, s, p, h, links, in0, stride, kk);
-  hop_k<P, R, 3, false, K>(acc, g, s, p, h, links, in0, stride, kk);
+  for (int k = 0; k < K; ++k) zero2(acc2[k]);
+  hop_k<P, R, 0, true, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 0, false, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 1, true, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 1, false, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 2, true, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 2, false, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 3, true, K>(acc2, g, s, p, h, links, in0, stride, kk);
+  hop_k<P, R, 3, false, K>(acc2, g, s, p, h, links, in0, stride, kk);
   const T dg = (T)diag;
   const bool read_diag = diag != 0.0;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     if (k >= kk) continue;
-    Spinor<T> d, res;
+    Spinor<T> d, res, acck;
+    unpair(acck, acc2[k]);
     if (read_diag) SpinorIO<P>::load(d, in0 + k * stride, g.Vh, p, h);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        cx<T> v = (T)(-0.5) * acc[k].s[a][c];
+        cx<T> v = (T)(-0.5) * acck.s[a][c];
         if (read_diag) v = v + dg * d.s[a][c];
         res.s[a][c] = a < 2 ? v : -v;
       }

@@ -7,6 +7,11 @@
 //     FP64: 12 chunks of double2;  FP32: 6 chunks of float4;  FP16: 3 chunks of 8 halves.
 //   chunk c of site (p, h) lives at index (p*NC + c)*Vh + h, so consecutive threads (consecutive h)
 //   read consecutive 16-byte words: every load is a coalesced 128-bit access.
+//   FP64 chunks hold the 12 complex components in canonical order.  FP32 and FP16 hold them in
+//   spin-row pairs, the operands of packed FP32 (f32x2) arithmetic: for colour i the pairs
+//   (s0.re, s1.re), (s0.im, s1.im) of the upper spins and (s2.re, s3.re), (s2.im, s3.im) of the
+//   lower spins.  FP32 chunk i < 3 = [(s0.re, s1.re), (s0.im, s1.im)] of colour i, chunk 3 + i the
+//   lower spins of colour i; FP16 stores the same 12 pairs in that order, four per chunk.
 //   FP16 fields carry one FP32 scale per site after the chunks (index p*Vh + h); the stored
 //   halves are value/scale with scale = max |component| of the site.
 // Internal link layout, for parity p and direction mu (U_mu(x) for x of parity p):
@@ -106,6 +111,31 @@ struct Spinor {
   cx<T> s[4][3];
 };
 
+// The same spinor as spin-row pairs for packed FP32 arithmetic: ur[i] = (s0[i].re, s1[i].re),
+// ui[i] = (s0[i].im, s1[i].im), dr[i] = (s2[i].re, s3[i].re), di[i] = (s2[i].im, s3[i].im).
+struct Spinor2 {
+  float2 ur[3], ui[3], dr[3], di[3];
+};
+
+__device__ __forceinline__ void unpair(Spinor<float>& v, const Spinor2& w) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    v.s[0][i] = mk(w.ur[i].x, w.ui[i].x);
+    v.s[1][i] = mk(w.ur[i].y, w.ui[i].y);
+    v.s[2][i] = mk(w.dr[i].x, w.di[i].x);
+    v.s[3][i] = mk(w.dr[i].y, w.di[i].y);
+  }
+}
+__device__ __forceinline__ void pair(Spinor2& w, const Spinor<float>& v) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    w.ur[i] = make_float2(v.s[0][i].re, v.s[1][i].re);
+    w.ui[i] = make_float2(v.s[0][i].im, v.s[1][i].im);
+    w.dr[i] = make_float2(v.s[2][i].re, v.s[3][i].re);
+    w.di[i] = make_float2(v.s[2][i].im, v.s[3][i].im);
+  }
+}
+
 // ------------------------------------------------------------------ spinor access
 template <int P>
 struct SpinorIO;
@@ -137,78 +167,111 @@ struct SpinorIO<P64> {
 template <>
 struct SpinorIO<P32> {
   using T = float;
-  __device__ __forceinline__ static void load(Spinor<T>& v, const void* base, int64_t Vh, int p, int64_t h) {
+  __device__ __forceinline__ static void load2(Spinor2& v, const void* base, int64_t Vh, int p, int64_t h) {
     const float4* b = reinterpret_cast<const float4*>(base) + (int64_t)p * 6 * Vh + h;
 #pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      float4 w = __ldg(b + c * Vh);
-      int k = 2 * c;  // complex index 0..11
-      v.s[k / 3][k % 3] = mk(w.x, w.y);
-      v.s[(k + 1) / 3][(k + 1) % 3] = mk(w.z, w.w);
+    for (int i = 0; i < 3; ++i) {
+      const float4 u = __ldg(b + i * Vh), d = __ldg(b + (3 + i) * Vh);
+      v.ur[i] = make_float2(u.x, u.y);
+      v.ui[i] = make_float2(u.z, u.w);
+      v.dr[i] = make_float2(d.x, d.y);
+      v.di[i] = make_float2(d.z, d.w);
+    }
+  }
+  __device__ __forceinline__ static void load(Spinor<T>& v, const void* base, int64_t Vh, int p, int64_t h) {
+    Spinor2 w;
+    load2(w, base, Vh, p, h);
+    unpair(v, w);
+  }
+  // chunks c with c % nparts == part
+  __device__ __forceinline__ static void store2(const Spinor2& v, void* base, int64_t Vh, int p, int64_t h,
+                                                int part = 0, int nparts = 1) {
+    float4* b = reinterpret_cast<float4*>(base) + (int64_t)p * 6 * Vh + h;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      if (i % nparts == part) b[i * Vh] = make_float4(v.ur[i].x, v.ur[i].y, v.ui[i].x, v.ui[i].y);
+      if ((3 + i) % nparts == part) b[(3 + i) * Vh] = make_float4(v.dr[i].x, v.dr[i].y, v.di[i].x, v.di[i].y);
     }
   }
   __device__ __forceinline__ static void store(const Spinor<T>& v, void* base, int64_t Vh, int p, int64_t h,
                                                int part = 0, int nparts = 1) {
-    float4* b = reinterpret_cast<float4*>(base) + (int64_t)p * 6 * Vh + h;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      if (c % nparts != part) continue;
-      int k = 2 * c;
-      cx<float> a = v.s[k / 3][k % 3], d = v.s[(k + 1) / 3][(k + 1) % 3];
-      b[c * Vh] = make_float4(a.re, a.im, d.re, d.im);
-    }
+    Spinor2 w;
+    pair(w, v);
+    store2(w, base, Vh, p, h, part, nparts);
   }
   __device__ __forceinline__ static bool owns(int a, int c, int part, int nparts) {
-    return ((3 * a + c) / 2) % nparts == part;
+    return (a < 2 ? c : 3 + c) % nparts == part;
   }
 };
 
 template <>
 struct SpinorIO<P16> {
   using T = float;
-  __device__ __forceinline__ static void load(Spinor<T>& v, const void* base, int64_t Vh, int p, int64_t h) {
+  // the 12 spin-row pairs in storage order: ur0 ui0 ur1 ui1 | ur2 ui2 dr0 di0 | dr1 di1 dr2 di2
+  __device__ __forceinline__ static float2& slot(Spinor2& v, int k) {
+    const int i = k >> 1;
+    return i < 3 ? ((k & 1) ? v.ui[i] : v.ur[i]) : ((k & 1) ? v.di[i - 3] : v.dr[i - 3]);
+  }
+  __device__ __forceinline__ static const float2& slot(const Spinor2& v, int k) {
+    const int i = k >> 1;
+    return i < 3 ? ((k & 1) ? v.ui[i] : v.ur[i]) : ((k & 1) ? v.di[i - 3] : v.dr[i - 3]);
+  }
+  __device__ __forceinline__ static void load2(Spinor2& v, const void* base, int64_t Vh, int p, int64_t h) {
     const uint4* b = reinterpret_cast<const uint4*>(base) + (int64_t)p * 3 * Vh + h;
     const float* sc = reinterpret_cast<const float*>(reinterpret_cast<const uint4*>(base) + 6 * Vh);
-    float s = __ldg(sc + (int64_t)p * Vh + h);
+    const float s = __ldg(sc + (int64_t)p * Vh + h);
+    const float2 ss = make_float2(s, s);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      uint4 w = __ldg(b + c * Vh);
-      unsigned u[4] = {w.x, w.y, w.z, w.w};
+      const uint4 w = __ldg(b + c * Vh);
+      const unsigned u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        __half2 hh = *reinterpret_cast<__half2*>(&u[j]);
-        float2 f = __half22float2(hh);
-        int k = 4 * c + j;
-        v.s[k / 3][k % 3] = mk(f.x * s, f.y * s);
+        __half2 hh = *reinterpret_cast<const __half2*>(&u[j]);
+        slot(v, 4 * c + j) = __fmul2_rn(__half22float2(hh), ss);
       }
     }
   }
-  __device__ __forceinline__ static void store(const Spinor<T>& v, void* base, int64_t Vh, int p, int64_t h,
-                                               int part = 0, int nparts = 1) {
+  __device__ __forceinline__ static void load(Spinor<T>& v, const void* base, int64_t Vh, int p, int64_t h) {
+    Spinor2 w;
+    load2(w, base, Vh, p, h);
+    unpair(v, w);
+  }
+  __device__ __forceinline__ static void store2(const Spinor2& v, void* base, int64_t Vh, int p, int64_t h,
+                                                int part = 0, int nparts = 1) {
     uint4* b = reinterpret_cast<uint4*>(base) + (int64_t)p * 3 * Vh + h;
     float* sc = reinterpret_cast<float*>(reinterpret_cast<uint4*>(base) + 6 * Vh);
     float mx = 0.f;
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int i = 0; i < 3; ++i) mx = fmaxf(mx, fmaxf(fabsf(v.s[a][i].re), fabsf(v.s[a][i].im)));
-    float inv = mx > 0.f ? 1.0f / mx : 0.f;
+    for (int k = 0; k < 12; ++k) {
+      const float2 f = slot(v, k);
+      mx = fmaxf(mx, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+    const float inv = mx > 0.f ? 1.0f / mx : 0.f;
+    const float2 ii = make_float2(inv, inv);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       if (c % nparts != part) continue;
       unsigned u[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        int k = 4 * c + j;
-        __half2 hh = __floats2half2_rn(v.s[k / 3][k % 3].re * inv, v.s[k / 3][k % 3].im * inv);
+        const float2 f = __fmul2_rn(slot(v, 4 * c + j), ii);
+        __half2 hh = __floats2half2_rn(f.x, f.y);
         u[j] = *reinterpret_cast<unsigned*>(&hh);
       }
       b[c * Vh] = make_uint4(u[0], u[1], u[2], u[3]);
     }
     if (part == 0) sc[(int64_t)p * Vh + h] = mx;
   }
+  __device__ __forceinline__ static void store(const Spinor<T>& v, void* base, int64_t Vh, int p, int64_t h,
+                                               int part = 0, int nparts = 1) {
+    Spinor2 w;
+    pair(w, v);
+    store2(w, base, Vh, p, h, part, nparts);
+  }
+  // pair k of component (a, c): spins 0, 1 -> 2c (re) and 2c + 1 (im); spins 2, 3 -> 6 + 2c ...
   __device__ __forceinline__ static bool owns(int a, int c, int part, int nparts) {
-    return ((3 * a + c) / 4) % nparts == part;
+    return (((a < 2 ? 0 : 6) + 2 * c) / 4) % nparts == part;
   }
 };
 

@@ -18,7 +18,30 @@ struct Geom {
   int Vh;          // sites per parity
   int apbc;        // 1: antiperiodic in time
   int even_only;   // BLAS-1 kernels: 1 = fields of the even sites only (parity 0), 0 = whole lattice
+  // division by L[1], L[2], L[3] as a multiply-high (set by geom_set_divisors): for a divisor d
+  // with l = ceil(log2 d), n / d = (t + ((n - t) >> 1)) >> (l - 1), t = umulhi(n, div_m),
+  // div_m = floor(2^32 (2^l - d) / d) + 1, exact for every 32-bit n (Granlund and Montgomery, 1994)
+  unsigned div_m[4];
+  int div_l[4];
 };
+
+// Fill the division constants of g for L[1..3] (all extents are even, so every l >= 1).
+__host__ inline void geom_set_divisors(Geom& g) {
+  for (int k = 1; k < 4; ++k) {
+    const unsigned d = (unsigned)g.L[k];
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    g.div_l[k] = l;
+    g.div_m[k] = (unsigned)((((1ull << l) - d) << 32) / d + 1);
+  }
+  g.div_l[0] = 0;
+  g.div_m[0] = 0;
+}
+
+__device__ __forceinline__ unsigned geom_div(unsigned n, const Geom& g, int k) {
+  const unsigned t = __umulhi(n, g.div_m[k]);
+  return (t + ((n - t) >> 1)) >> (g.div_l[k] - 1);
+}
 
 // Sites a BLAS-1 launch covers: parity 0 comes first in every field layout, so an even-site field
 // is the first half of a whole-lattice one.
@@ -32,11 +55,11 @@ struct Site {
 __device__ __forceinline__ Site site_of(const Geom& g, int p, int h) {
   Site s;
   unsigned twoh = 2u * (unsigned)h;
-  unsigned q = twoh / (unsigned)g.L[3];
+  unsigned q = geom_div(twoh, g, 3);
   unsigned r3 = twoh - q * (unsigned)g.L[3];
-  unsigned q2 = q / (unsigned)g.L[2];
+  unsigned q2 = geom_div(q, g, 2);
   s.x[2] = (int)(q - q2 * (unsigned)g.L[2]);
-  unsigned q1 = q2 / (unsigned)g.L[1];
+  unsigned q1 = geom_div(q2, g, 1);
   s.x[1] = (int)(q2 - q1 * (unsigned)g.L[1]);
   s.x[0] = (int)q1;
   int b = (p + s.x[0] + s.x[1] + s.x[2]) & 1;

@@ -13,6 +13,7 @@
 // Stopping: shift l freezes once |zeta_l'| ||r|| <= tol_l ||b||; the run ends after the
 // iteration in which the last shift froze (CG_PENDING), or at once on a breakdown / NaN
 // (CG_DONE), or after maxit iterations (CG_PENDING with ND_ERR_NOT_CONVERGED).
+#include <algorithm>
 #include <math.h>
 
 #include "../../include/nd.h"
@@ -281,30 +282,36 @@ __global__ void bcg_scalar_kernel(double* states, int nsys, int maxit, cudaGraph
   if (GRAPH && threadIdx.x == 0 && !running) cudaGraphSetConditional(h, 0);
 }
 
+// x += alpha p, p = r + beta p for every system that has not stopped.  A grid of resident blocks
+// strides over the (site block, system) items; the items of stopped systems cost one flag read.
 template <int PS>
 __global__ void __launch_bounds__(256) bcg_update_kernel(const Geom g, const char* r, char* p, char* x, size_t fstride,
-                                                         const double* states) {
+                                                         const double* states, int nsys) {
   using T = typename Traits<PS>::real;
-  const double* st = states + (int64_t)blockIdx.y * CG_STATE_DOUBLES;
-  if (st[CG_DONE] != 0.0) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * g.Vh) return;
-  const int pp = i >= g.Vh ? 1 : 0, h = i - pp * g.Vh;
-  const size_t off = (size_t)blockIdx.y * fstride;
-  Spinor<T> vr, vp, vx;
-  SpinorIO<PS>::load(vr, r + off, g.Vh, pp, h);
-  SpinorIO<PS>::load(vp, p + off, g.Vh, pp, h);
-  SpinorIO<PS>::load(vx, x + off, g.Vh, pp, h);
-  const T a = (T)st[sh(SH_COEFX, 0)], b = (T)st[sh(SH_COEFP, 0)];
+  const int bps = (2 * g.Vh + 255) / 256;
+  for (int item = blockIdx.x; item < bps * nsys; item += gridDim.x) {
+    const int sys = item % nsys, blk = item / nsys;
+    const double* st = states + (int64_t)sys * CG_STATE_DOUBLES;
+    if (st[CG_DONE] != 0.0) continue;
+    const int i = blk * 256 + threadIdx.x;
+    if (i >= 2 * g.Vh) continue;
+    const int pp = i >= g.Vh ? 1 : 0, h = i - pp * g.Vh;
+    const size_t off = (size_t)sys * fstride;
+    Spinor<T> vr, vp, vx;
+    SpinorIO<PS>::load(vr, r + off, g.Vh, pp, h);
+    SpinorIO<PS>::load(vp, p + off, g.Vh, pp, h);
+    SpinorIO<PS>::load(vx, x + off, g.Vh, pp, h);
+    const T a = (T)st[sh(SH_COEFX, 0)], b = (T)st[sh(SH_COEFP, 0)];
 #pragma unroll
-  for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < 4; ++s)
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      vx.s[s][c] = vx.s[s][c] + a * vp.s[s][c];
-      vp.s[s][c] = vr.s[s][c] + b * vp.s[s][c];
-    }
-  SpinorIO<PS>::store(vx, x + off, g.Vh, pp, h);
-  SpinorIO<PS>::store(vp, p + off, g.Vh, pp, h);
+      for (int c = 0; c < 3; ++c) {
+        vx.s[s][c] = vx.s[s][c] + a * vp.s[s][c];
+        vp.s[s][c] = vr.s[s][c] + b * vp.s[s][c];
+      }
+    SpinorIO<PS>::store(vx, x + off, g.Vh, pp, h);
+    SpinorIO<PS>::store(vp, p + off, g.Vh, pp, h);
+  }
 }
 
 cudaError_t bcg_init(double* states, int nsys, cudaStream_t st) {
@@ -324,14 +331,20 @@ cudaError_t bcg_scalar(double* states, int nsys, int maxit, const cudaGraphCondi
 
 cudaError_t bcg_update(const Geom& g, int ps, const void* r, void* p, void* x, size_t fstride, const double* states,
                        int nsys, cudaStream_t st) {
-  const dim3 grid((2 * g.Vh + 255) / 256, nsys);
+  // one wave of resident 256-thread blocks (4 per SM), capped by the number of items
+  static int sms[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && sms[dev] == 0) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  const int64_t items = (int64_t)((2 * g.Vh + 255) / 256) * nsys;
+  const int grid = (int)std::min<int64_t>(items, 4 * (int64_t)std::max(1, dev < 64 ? sms[dev] : 152));
   const char* rr = static_cast<const char*>(r);
   char* pp = static_cast<char*>(p);
   char* xx = static_cast<char*>(x);
   switch (ps) {
-    case P64: bcg_update_kernel<P64><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
-    case P32: bcg_update_kernel<P32><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
-    case P16: bcg_update_kernel<P16><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states); break;
+    case P64: bcg_update_kernel<P64><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states, nsys); break;
+    case P32: bcg_update_kernel<P32><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states, nsys); break;
+    case P16: bcg_update_kernel<P16><<<grid, 256, 0, st>>>(g, rr, pp, xx, fstride, states, nsys); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
