@@ -485,7 +485,7 @@ def dn_oracle_check(nd, torch, reps, peak):
     return res
 
 
-def dn_phase(nd, torch, reps, peak):
+def dn_phase(nd, torch, reps, peak, dynamic_l=True):
     """D_N applies/s: 16^3x32 Haar links, 20 poles, 20 deflated low modes, rational part to 1e-10."""
     import numpy as np
 
@@ -553,31 +553,32 @@ def dn_phase(nd, torch, reps, peak):
     res["propagator"] = {"s": round(t, 3), "cg_iters": pinf.iters, "passes": pinf.outer,
                          "sign_krylov_iters": pinf.sign_iters,
                          "resid": pinf.resid, "m_q": 0.1, "inner": "mixed_fp32, sign to 1e-12"}
-    # the paper's error control: l chosen in [12, 24] by the largest relative gap, modes refined until
-    # kappa_+- <= 1e-2 (projector deviation <= ~1e-2); then the mixed FP32 D_N with those modes (eps from
-    # the chosen lambda_{l+1})
-    t0 = time.perf_counter()
-    ld, _, _, _, lid = nd.nd_lowmodes_dynamic(ctx, 12, 24, 1e-2, 20000000)
-    t_dyn = time.perf_counter() - t0
-    kmax = max(lid.kappa_plus, lid.kappa_minus)
-    kk = kmax * (1 + 2 * kmax)
-    dyn = {"l": ld, "s": round(t_dyn, 3), "q2_applications": lid.iters, "kappa_plus": lid.kappa_plus,
-           "kappa_minus": lid.kappa_minus, "projector_bound": kk / (1 - 2 * kk) if 2 * kk < 1 else None,
-           "lambda_next": lid.lambda_next, "lambda_max": lid.lambda_max}
-    p = nd.dn_params(20, 0.0, 0.0, 1e-10, 200000, 1, 0.0, False)
-    o = torch.empty_like(eta)
-    nd.nd_apply_DN(ctx, o, eta, p)
-    torch.cuda.synchronize()
-    ts = []
-    for _ in range(reps):
+    if dynamic_l:
+        # the paper's error control: l chosen in [12, 24] by the largest relative gap, modes refined until
+        # kappa_+- <= 1e-2 (projector deviation <= ~1e-2); then the mixed FP32 D_N with those modes (eps from
+        # the chosen lambda_{l+1})
         t0 = time.perf_counter()
-        info = nd.nd_apply_DN(ctx, o, eta, p)
+        ld, _, _, _, lid = nd.nd_lowmodes_dynamic(ctx, 12, 24, 1e-2, 20000000)
+        t_dyn = time.perf_counter() - t0
+        kmax = max(lid.kappa_plus, lid.kappa_minus)
+        kk = kmax * (1 + 2 * kmax)
+        dyn = {"l": ld, "s": round(t_dyn, 3), "q2_applications": lid.iters, "kappa_plus": lid.kappa_plus,
+               "kappa_minus": lid.kappa_minus, "projector_bound": kk / (1 - 2 * kk) if 2 * kk < 1 else None,
+               "lambda_next": lid.lambda_next, "lambda_max": lid.lambda_max}
+        p = nd.dn_params(20, 0.0, 0.0, 1e-10, 200000, 1, 0.0, False)
+        o = torch.empty_like(eta)
+        nd.nd_apply_DN(ctx, o, eta, p)
         torch.cuda.synchronize()
-        ts.append(time.perf_counter() - t0)
-    t = float(np.median(ts))
-    dyn["mixed_fp32"] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "eps": info.eps,
-                         "krylov_iters": info.iters, "refinement_sweeps": info.outer}
-    res["dynamic_l"] = dyn
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            info = nd.nd_apply_DN(ctx, o, eta, p)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        t = float(np.median(ts))
+        dyn["mixed_fp32"] = {"applies_per_s": round(1.0 / t, 4), "s_per_apply": round(t, 4), "eps": info.eps,
+                             "krylov_iters": info.iters, "refinement_sweeps": info.outer}
+        res["dynamic_l"] = dyn
     base = outs["fp64"]
     for name in ("mixed_fp32", "mixed_fp16", "poly_fp64", "poly_fp32"):
         res[name]["rel_diff_vs_fp64"] = float(torch.linalg.vector_norm(outs[name] - base) /
@@ -846,6 +847,8 @@ def main():
     ap.add_argument("--dn-reps", type=int, default=2)
     ap.add_argument("--no-oracle-dn", action="store_true",
                     help="skip the D_N comparison with the FP64 oracle (about a minute of host time)")
+    ap.add_argument("--no-dynamic-l", action="store_true",
+                    help="skip the kappa-controlled low-mode leg of the D_N phase (about 100 s)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--case", default=None,
                     help="run a small profiling case and exit (hop24, hop24_fp16, clen24, dn16, dn16_fp64, dn16_fp16)")
@@ -904,7 +907,7 @@ def main():
     if not args.no_sweep:
         line["sweep"] = sweep_phase(nd, torch)
     if not args.no_dn:
-        line["dn"] = dn_phase(nd, torch, args.dn_reps, peak)
+        line["dn"] = dn_phase(nd, torch, args.dn_reps, peak, not args.no_dynamic_l)
         if not args.no_oracle_dn:
             line["dn"]["oracle_check"] = dn_oracle_check(nd, torch, args.dn_reps, peak)
         line["clenshaw"] = clenshaw_phase(nd, torch)

@@ -49,6 +49,139 @@ __device__ __forceinline__ void hopping_part(Spinor<typename Traits<P>::real>& a
   }
 }
 
+// Epilogue of the FP32 / FP16 operator on spin-row pairs, specialised at compile time on whether
+// the diagonal term (RD) and the y term (HY) are present: the same operations as the scalar
+// epilogue below, each on a pair (s0, s1) or (s2, s3) in one f32x2 instruction.  The runtime
+// choice between the four forms is taken once per thread, outside the unrolled loops (branches on
+// these flags inside the per-component loop measured 40 % slower).
+template <int P, int BASE, bool REDUCE, bool RD, bool HY>
+__device__ __forceinline__ void pairs_tail(const Geom& g, const QLaunch& A, Spinor2& v, int p, int h,
+                                           double (&red)[2]) {
+  const double a_d = BASE == Q_CGUPDATE ? A.cgs[CG_ASCALE] : A.a;
+  const double b_d = BASE == Q_CGUPDATE ? A.cgs[CG_SIGMA0] : A.b;
+  const float ca = (float)a_d;
+  const float2 mh = f2_bcast(-0.5f), dg = f2_bcast((float)A.diag), cb = f2_bcast((float)b_d);
+  const float2 cu = f2_bcast(ca), cl = f2_bcast(A.no_g5 ? ca : -ca);
+  // the vectors are folded in one at a time, so at most two spinors are live
+  float2 s1 = f2_bcast(0.f);
+  {
+    Spinor2 d;
+    if (RD) SpinorIO<P>::load2(d, A.din ? A.din : A.in, g.Vh, p, h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v.ur[c] = __fmul2_rn(mh, v.ur[c]);
+      v.ui[c] = __fmul2_rn(mh, v.ui[c]);
+      v.dr[c] = __fmul2_rn(mh, v.dr[c]);
+      v.di[c] = __fmul2_rn(mh, v.di[c]);
+      if (RD) {
+        v.ur[c] = f2_fma(dg, d.ur[c], v.ur[c]);
+        v.ui[c] = f2_fma(dg, d.ui[c], v.ui[c]);
+        v.dr[c] = f2_fma(dg, d.dr[c], v.dr[c]);
+        v.di[c] = f2_fma(dg, d.di[c], v.di[c]);
+        if (REDUCE && BASE != Q_CGUPDATE) {  // the CG update's second result is not used
+          s1 = f2_fma(d.ur[c], d.ur[c], s1);
+          s1 = f2_fma(d.ui[c], d.ui[c], s1);
+          s1 = f2_fma(d.dr[c], d.dr[c], s1);
+          s1 = f2_fma(d.di[c], d.di[c], s1);
+        }
+      }
+      v.ur[c] = __fmul2_rn(cu, v.ur[c]);
+      v.ui[c] = __fmul2_rn(cu, v.ui[c]);
+      v.dr[c] = __fmul2_rn(cl, v.dr[c]);
+      v.di[c] = __fmul2_rn(cl, v.di[c]);
+    }
+  }
+  // v += coef * x for one more input field x
+  auto fold = [&](const void* src, float2 coef) {
+    Spinor2 x;
+    SpinorIO<P>::load2(x, src, g.Vh, p, h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v.ur[c] = f2_fma(coef, x.ur[c], v.ur[c]);
+      v.ui[c] = f2_fma(coef, x.ui[c], v.ui[c]);
+      v.dr[c] = f2_fma(coef, x.dr[c], v.dr[c]);
+      v.di[c] = f2_fma(coef, x.di[c], v.di[c]);
+    }
+  };
+  if (HY) fold(A.y, cb);
+  if (BASE == Q_XPAY2 || BASE == Q_XPAY3) fold(A.z, f2_bcast((float)A.c));
+  if (BASE == Q_XPAY3) fold(A.w, f2_bcast((float)A.d));
+  if (BASE == Q_CGUPDATE) {
+    // out = out - alpha (v + b y), in place
+    const float2 nal = f2_bcast(-(float)(A.cgs[CG_RR] / (a_d * A.cgs[CG_TT] + b_d * A.cgs[CG_PP])));
+    Spinor2 z;
+    SpinorIO<P>::load2(z, A.out, g.Vh, p, h);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      v.ur[c] = f2_fma(nal, v.ur[c], z.ur[c]);
+      v.ui[c] = f2_fma(nal, v.ui[c], z.ui[c]);
+      v.dr[c] = f2_fma(nal, v.dr[c], z.dr[c]);
+      v.di[c] = f2_fma(nal, v.di[c], z.di[c]);
+    }
+  }
+  SpinorIO<P>::store2(v, A.out, g.Vh, p, h);
+  if (REDUCE) {
+    float2 s0 = f2_bcast(0.f);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      s0 = f2_fma(v.ur[c], v.ur[c], s0);
+      s0 = f2_fma(v.ui[c], v.ui[c], s0);
+      s0 = f2_fma(v.dr[c], v.dr[c], s0);
+      s0 = f2_fma(v.di[c], v.di[c], s0);
+    }
+    red[0] = (double)s0.x + (double)s0.y;
+    red[1] = (double)s1.x + (double)s1.y;
+  }
+}
+
+// The FP32 / FP16 operator of one thread on spin-row pairs (one warp per site, SPLIT == 1).
+template <int P, int R, int MODE, bool REDUCE>
+__device__ __forceinline__ void q_site_pairs(const Geom& g, const QLaunch& A, const ReduceSlot& slot, int blk,
+                                             int nblk, bool act, int p, int h) {
+  constexpr int BASE = (MODE == Q_MRHS || MODE == Q_BPLAIN) ? Q_PLAIN : (MODE == Q_BCG ? Q_CGUPDATE : MODE);
+  if (!REDUCE && !act) return;
+  double red[2] = {0.0, 0.0};
+  if (act) {
+    const Site s = site_of(g, p, h);
+    Spinor2 acc;
+    zero2(acc);
+    const char* L = static_cast<const char*>(A.links);
+    hop2<P, R, 0, true>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 0, false>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 1, true>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 1, false>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 2, true>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 2, false>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 3, true>(acc, g, s, p, h, L, A.in);
+    hop2<P, R, 3, false>(acc, g, s, p, h, L, A.in);
+    const bool rd = REDUCE || A.diag != 0.0;
+    if constexpr (BASE != Q_PLAIN) {
+      if (rd)
+        pairs_tail<P, BASE, REDUCE, true, true>(g, A, acc, p, h, red);
+      else
+        pairs_tail<P, BASE, REDUCE, false, true>(g, A, acc, p, h, red);
+    } else if constexpr (REDUCE) {
+      if (A.y)
+        pairs_tail<P, BASE, REDUCE, true, true>(g, A, acc, p, h, red);
+      else
+        pairs_tail<P, BASE, REDUCE, true, false>(g, A, acc, p, h, red);
+    } else {
+      if (A.y) {
+        if (rd)
+          pairs_tail<P, BASE, REDUCE, true, true>(g, A, acc, p, h, red);
+        else
+          pairs_tail<P, BASE, REDUCE, false, true>(g, A, acc, p, h, red);
+      } else {
+        if (rd)
+          pairs_tail<P, BASE, REDUCE, true, false>(g, A, acc, p, h, red);
+        else
+          pairs_tail<P, BASE, REDUCE, false, false>(g, A, acc, p, h, red);
+      }
+    }
+  }
+  if (REDUCE) grid_sum<2>(red, slot, nblk, blk);
+}
+
 // One block's share of a launch: the SITES output sites of block index blk of nblk (for the
 // multi-RHS and batched modes, blk runs over RHS fastest, then site blocks).
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS>
@@ -91,6 +224,10 @@ __device__ __forceinline__ void q_block(const Geom& g, const QLaunch& A0, int bl
   } else {
     p = A.parity0;
     h = i;
+  }
+  if constexpr (P != P64 && SPLIT == 1) {
+    q_site_pairs<P, R, MODE, REDUCE>(g, A, slot, blk, nblk, act, p, h);
+    return;
   }
   Site s;
   if (act) s = site_of(g, p, h);
