@@ -43,8 +43,9 @@ __global__ void __launch_bounds__(BT_THREADS, 8) q_batched_kernel(const LatticeW
     const int local = t - begin[k];
     const int r = local % w.nrhs, blk = local / w.nrhs;
     const int i = blk * BT_THREADS + threadIdx.x;
-    if (i >= 2 * w.g.Vh) continue;
-    const int p = i & 1, h = i >> 1;
+    int p, h;
+    both_parities_site(i, &p, &h);
+    if (h >= w.g.Vh) continue;
     q_site<P, R>(w.g, w.links, static_cast<const char*>(w.in) + r * w.stride, static_cast<char*>(w.out) + r * w.stride,
                  w.diag, p, h);
   }

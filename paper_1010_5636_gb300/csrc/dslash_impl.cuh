@@ -214,13 +214,13 @@ __device__ __forceinline__ void q_block(const Geom& g, const QLaunch& A0, int bl
   // every block of one system sees the same flags, so whole reductions are skipped together
   if (A.cgs && (A.cgs[CG_DONE] != 0.0 || A.cgs[CG_PENDING] != 0.0)) return;
   const int i = blk * SITES + jloc;
-  const bool act = i < A.nsites;
+  bool act = i < A.nsites;
   int p = 0, h = 0;
   if (A.nsites == 2 * g.Vh) {
-    // both parities: neighbouring threads take the even and odd site of the same h, so a
+    // both parities: the warps of a pair take the even and odd sites of the same h range, so a
     // link or spinor used by both parities is read from DRAM once while it is still in L2
-    p = i & 1;
-    h = i >> 1;
+    both_parities_site(i, &p, &h);
+    act = h < g.Vh;
   } else {
     p = A.parity0;
     h = i;
@@ -337,11 +337,45 @@ __device__ __forceinline__ void q_block(const Geom& g, const QLaunch& A0, int bl
 template <int P, int R, int MODE, bool REDUCE, int SPLIT, int THREADS = Q_THREADS, int MINB = 1>
 __global__ void __launch_bounds__(THREADS, MINB) q_kernel(const Geom g, const QLaunch A0) {
   if constexpr (MODE == Q_BPLAIN || MODE == Q_BCG) {
-    // batched systems: a grid of resident blocks strides over the (system, site block) items, so
-    // the items of systems that have stopped cost one flag read each instead of a block launch
+    // batched systems: a grid of resident blocks strides over the (running system, site block)
+    // items, running systems fastest.  Each block first lists the systems that have not stopped
+    // (their flags do not change during the launch), so a stopped system costs neither a block
+    // launch nor a flag read per item.
     constexpr int SITES = THREADS / SPLIT;
-    const int items = (A0.nsites + SITES - 1) / SITES * A0.nrhs;
-    for (int item = blockIdx.x; item < items; item += gridDim.x) q_block<P, R, MODE, REDUCE, SPLIT, THREADS>(g, A0, item, items);
+    __shared__ short running[ND_BATCH_MAX_SYSTEMS];
+    __shared__ int nrun;
+    if (threadIdx.x < 32) {
+      int base = 0;
+      for (int c = 0; c < A0.nrhs; c += 32) {
+        const int sys = c + (int)threadIdx.x;
+        bool go = false;
+        if (sys < A0.nrhs) {
+          const double* st = A0.cgs + (int64_t)sys * A0.cgs_stride;
+          go = st[CG_DONE] == 0.0 && st[CG_PENDING] == 0.0;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, go);
+        if (go) running[base + __popc(m & ((1u << threadIdx.x) - 1u))] = (short)sys;
+        base += __popc(m);
+      }
+      if (threadIdx.x == 0) nrun = base;
+    }
+    __syncthreads();
+    const int nr = nrun, bps = (A0.nsites + SITES - 1) / SITES;
+    for (int item = blockIdx.x; item < nr * bps; item += gridDim.x) {
+      const int sys = running[item % nr], blk = item / nr;
+      q_block<P, R, MODE, REDUCE, SPLIT, THREADS>(g, A0, blk * A0.nrhs + sys, bps * A0.nrhs);
+    }
+  } else if constexpr (P != P64 && SPLIT == 1 && MODE != Q_MRHS) {
+    // one system, one warp per site: straight from the launch parameters to the packed path
+    if (A0.cgs && (A0.cgs[CG_DONE] != 0.0 || A0.cgs[CG_PENDING] != 0.0)) return;
+    const int i = blockIdx.x * THREADS + threadIdx.x;
+    int p = A0.parity0, h = i;
+    bool act = i < A0.nsites;
+    if (A0.nsites == 2 * g.Vh) {
+      both_parities_site(i, &p, &h);
+      act = h < g.Vh;
+    }
+    q_site_pairs<P, R, MODE, REDUCE>(g, A0, A0.slot, blockIdx.x, gridDim.x, act, p, h);
   } else {
     q_block<P, R, MODE, REDUCE, SPLIT, THREADS>(g, A0, blockIdx.x, gridDim.x);
   }

@@ -46,7 +46,7 @@ __device__ __forceinline__ void hop_k(Spinor2 (&acc)[K], const Geom& g, const Si
 }
 
 // out_r = gamma5 (diag in_r - 1/2 hop(in_r)) for r < nrhs (fields at + r * stride bytes), output sites
-// of both parities (nsites = 2 Vh, interleaved as in q_kernel) or of parity0 only (nsites = Vh).
+// of both parities (nsites = 2 Vh, parity alternating by warp as in q_kernel) or of parity0 only (nsites = Vh).
 template <int P, int R, int K>
 __global__ void __launch_bounds__(MR_THREADS, MR_MIN_BLOCKS)
     q_mrhs_kernel(const Geom g, const char* links, const char* in, char* out, int64_t stride, int nrhs, int nsites,
@@ -57,15 +57,10 @@ __global__ void __launch_bounds__(MR_THREADS, MR_MIN_BLOCKS)
   const int r0 = grp * K;
   const int kk = min(K, nrhs - r0);
   const int i = blk * MR_THREADS + threadIdx.x;
-  if (i >= nsites) return;
-  int p, h;
-  if (nsites == 2 * g.Vh) {
-    p = i & 1;
-    h = i >> 1;
-  } else {
-    p = parity0;
-    h = i;
-  }
+  int p = parity0, h = i;
+  if (nsites == 2 * g.Vh)
+    both_parities_site(i, &p, &h);
+  if (h >= g.Vh) return;
   const Site s = site_of(g, p, h);
   const char* in0 = in + r0 * stride;
   char* out0 = out + r0 * stride;

@@ -68,6 +68,15 @@ __device__ __forceinline__ Site site_of(const Geom& g, int p, int h) {
   return s;
 }
 
+// Output site of thread slot i in a launch over both parities: runs of 32 slots alternate
+// parity over the same 32 half indices, p = (i / 32) mod 2, h = 32 (i / 64) + i mod 32.  Each warp
+// thus reads one contiguous, aligned run of every field, and the two warps of a pair use the links
+// and neighbours of one h range while they are still in cache.  Slots with h >= Vh are idle.
+__host__ __device__ __forceinline__ void both_parities_site(int i, int* p, int* h) {
+  *p = (i >> 5) & 1;
+  *h = ((i >> 6) << 5) | (i & 31);
+}
+
 // Half index of the neighbour x + mu (fwd) or x - mu (bwd); *crossed = 1 if the hop wraps
 // around the time boundary (for antiperiodic boundary conditions).
 template <int MU, bool FWD>

@@ -35,6 +35,9 @@ enum CgArray {
   SH_W, SH_NARRAY
 };
 constexpr int CG_NMAX = 32;
+// Largest number of systems of one batched CG (the batched Q and update kernels list them in
+// shared memory).
+constexpr int ND_BATCH_MAX_SYSTEMS = 1024;
 constexpr int CG_STATE_DOUBLES = CG_NSCALAR + SH_NARRAY * CG_NMAX;
 __host__ __device__ inline int sh(int array, int l) { return CG_NSCALAR + array * CG_NMAX + l; }
 

@@ -283,16 +283,30 @@ __global__ void bcg_scalar_kernel(double* states, int nsys, int maxit, cudaGraph
 }
 
 // x += alpha p, p = r + beta p for every system that has not stopped.  A grid of resident blocks
-// strides over the (site block, system) items; the items of stopped systems cost one flag read.
+// strides over the (site block, running system) items.
 template <int PS>
 __global__ void __launch_bounds__(256) bcg_update_kernel(const Geom g, const char* r, char* p, char* x, size_t fstride,
                                                          const double* states, int nsys) {
   using T = typename Traits<PS>::real;
-  const int bps = (2 * g.Vh + 255) / 256;
-  for (int item = blockIdx.x; item < bps * nsys; item += gridDim.x) {
-    const int sys = item % nsys, blk = item / nsys;
+  // the systems still updating (CG_DONE does not change during the launch), listed once per block
+  __shared__ short running[ND_BATCH_MAX_SYSTEMS];
+  __shared__ int nrun;
+  if (threadIdx.x < 32) {
+    int base = 0;
+    for (int c = 0; c < nsys; c += 32) {
+      const int sys = c + (int)threadIdx.x;
+      const bool go = sys < nsys && states[(int64_t)sys * CG_STATE_DOUBLES + CG_DONE] == 0.0;
+      const unsigned m = __ballot_sync(0xffffffffu, go);
+      if (go) running[base + __popc(m & ((1u << threadIdx.x) - 1u))] = (short)sys;
+      base += __popc(m);
+    }
+    if (threadIdx.x == 0) nrun = base;
+  }
+  __syncthreads();
+  const int bps = (2 * g.Vh + 255) / 256, nr = nrun;
+  for (int item = blockIdx.x; item < bps * nr; item += gridDim.x) {
+    const int sys = running[item % nr], blk = item / nr;
     const double* st = states + (int64_t)sys * CG_STATE_DOUBLES;
-    if (st[CG_DONE] != 0.0) continue;
     const int i = blk * 256 + threadIdx.x;
     if (i >= 2 * g.Vh) continue;
     const int pp = i >= g.Vh ? 1 : 0, h = i - pp * g.Vh;

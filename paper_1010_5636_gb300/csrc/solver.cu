@@ -260,7 +260,7 @@ nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<d
                   const std::vector<double>& tol, double ascale, int maxit, std::vector<int>* iters) {
   NvtxRange range("nd.batched_cg");
   const int nsys = (int)sigma.size();
-  if (nsys < 1 || nsys > 1024) return fail(c, ND_ERR_INVALID_ARG, "batched CG: 1..1024 systems");
+  if (nsys < 1 || nsys > ND_BATCH_MAX_SYSTEMS) return fail(c, ND_ERR_INVALID_ARG, "batched CG: 1..1024 systems");
   if (!c->links[ps]) return fail(c, ND_ERR_STATE, "batched CG: links not set in the Krylov precision");
   const size_t fs = (size_t)spinor_bytes(ps, c->Vh);
   char* r = static_cast<char*>(field(c, "bc_r", ps, nsys));
