@@ -459,11 +459,11 @@ static cudaError_t launch_q2(const Geom& g, const QLaunch& L, cudaStream_t st) {
     case Q_BPLAIN:
       if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64) return launch_q5<P, R, Q_BPLAIN, true, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, Q_BPLAIN, true, 1, 64, 8>(g, L, st);
+      return launch_q5<P, R, Q_BPLAIN, true, 1, 256, 2>(g, L, st);
     case Q_BCG:
       if (!L.reduce || L.split != 1) return cudaErrorInvalidValue;
       if (P == P64) return launch_q5<P, R, Q_BCG, true, 1, 256, 1>(g, L, st);
-      return launch_q5<P, R, Q_BCG, true, 1, 64, 8>(g, L, st);
+      return launch_q5<P, R, Q_BCG, true, 1, 256, 2>(g, L, st);
   }
   return cudaErrorInvalidValue;
 }
