@@ -142,6 +142,12 @@ void nd_destroy(nd_ctx* c) {
     if (gr.exec) cudaGraphExecDestroy(gr.exec);
     if (gr.graph) cudaGraphDestroy(gr.graph);
   }
+  if (c->aux_stream) {
+    cudaStreamSynchronize(c->aux_stream);
+    cudaStreamDestroy(c->aux_stream);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
+  if (c->join_ev) cudaEventDestroy(c->join_ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   for (auto& kv : c->ws) cudaFree(kv.second.first);
   if (c->evecs) cudaFree(c->evecs);

@@ -53,6 +53,10 @@ struct nd_ctx {
   // captured multi-shift iterations (graphs_ok = false after a capture failure, or with ND_GRAPHS=0 in
   // the environment: chunked launches from the host)
   cudaStream_t cap_stream = nullptr;
+  // second stream of the mixed-precision refinement (the slowest shifts' first correction runs on it
+  // while the other shifts are refined on `stream`), with its fork and join events
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   std::vector<nd_ms_graph> ms_graphs;
   bool graphs_ok = true;
 };

@@ -45,15 +45,17 @@ void* field(nd_ctx* c, const char* name, int prec, int count) {
   return workspace(c, name, (size_t)spinor_bytes(prec, c->Vh) * (size_t)count);
 }
 
-nd_status read_back(nd_ctx* c, const double* dev, double* host, int n) {
+nd_status read_back_on(nd_ctx* c, cudaStream_t st, const double* dev, double* host, int n) {
   for (int k0 = 0; k0 < n; k0 += ND_PINNED_DOUBLES) {
     const int k = std::min(ND_PINNED_DOUBLES, n - k0);
-    ND_TRY_CUDA(c, cudaMemcpyAsync(c->host_pinned, dev + k0, sizeof(double) * k, cudaMemcpyDeviceToHost, c->stream));
-    ND_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    ND_TRY_CUDA(c, cudaMemcpyAsync(c->host_pinned, dev + k0, sizeof(double) * k, cudaMemcpyDeviceToHost, st));
+    ND_TRY_CUDA(c, cudaStreamSynchronize(st));
     std::copy(c->host_pinned, c->host_pinned + k, host + k0);
   }
   return ND_OK;
 }
+
+nd_status read_back(nd_ctx* c, const double* dev, double* host, int n) { return read_back_on(c, c->stream, dev, host, n); }
 
 // One multi-shift CG iteration (K1..K4, see mscg.cu) launched on stream st; with graph != null
 // the scalar kernel also drives the graph's while-loop condition.
@@ -256,19 +258,26 @@ static cudaError_t bcg_iteration(nd_ctx* c, cudaStream_t st, int ps, char* r, ch
 
 // Solve (ascale Q^2 + sigma_s) x_s = b_s for s < nsys (independent systems run in lockstep: one
 // multi-RHS Q launch per step for all of them).  b, x: nsys consecutive fields of precision ps.
-nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<double>& sigma,
-                  const std::vector<double>& tol, double ascale, int maxit, std::vector<int>* iters) {
+// bcg_start issues the solve on `stream` with workspaces named after `tag` (two solves with
+// different tags may run at the same time on different streams: they share no buffer, counter or
+// reduction scratch); with graphs the iterations run on the device and bcg_finish reads the result
+// back, without graphs the host loop runs inside bcg_start.
+nd_status bcg_start(nd_ctx* c, int ps, const void* b, void* x, const std::vector<double>& sigma,
+                    const std::vector<double>& tol, double ascale, int maxit, const std::string& tag,
+                    cudaStream_t stream, BcgJob* job) {
   NvtxRange range("nd.batched_cg");
   const int nsys = (int)sigma.size();
   if (nsys < 1 || nsys > ND_BATCH_MAX_SYSTEMS) return fail(c, ND_ERR_INVALID_ARG, "batched CG: 1..1024 systems");
   if (!c->links[ps]) return fail(c, ND_ERR_STATE, "batched CG: links not set in the Krylov precision");
   const size_t fs = (size_t)spinor_bytes(ps, c->Vh);
-  char* r = static_cast<char*>(field(c, "bc_r", ps, nsys));
-  char* t = static_cast<char*>(field(c, "bc_t", ps, nsys));
-  char* p = static_cast<char*>(field(c, "bc_p", ps, nsys));
-  double* states = static_cast<double*>(workspace(c, "bc_state", sizeof(double) * CG_STATE_DOUBLES * nsys));
-  double* partials = static_cast<double*>(workspace(c, "bc_partials", sizeof(double) * bcg_partials(c->g, ps, nsys)));
-  unsigned* counters = static_cast<unsigned*>(workspace(c, "bc_counters", sizeof(unsigned) * nsys));
+  char* r = static_cast<char*>(field(c, (tag + "_r").c_str(), ps, nsys));
+  char* t = static_cast<char*>(field(c, (tag + "_t").c_str(), ps, nsys));
+  char* p = static_cast<char*>(field(c, (tag + "_p").c_str(), ps, nsys));
+  double* states = static_cast<double*>(workspace(c, tag + "_state", sizeof(double) * CG_STATE_DOUBLES * nsys));
+  double* partials =
+      static_cast<double*>(workspace(c, tag + "_partials", sizeof(double) * bcg_partials(c->g, ps, nsys)));
+  // one counter per system for the batched launches, one more for the set-up reductions
+  unsigned* counters = static_cast<unsigned*>(workspace(c, tag + "_counters", sizeof(unsigned) * (nsys + 1)));
   if (!r || !t || !p || !states || !partials || !counters) return fail(c, ND_ERR_OOM, "batched CG: workspace");
   std::vector<double> h((size_t)CG_STATE_DOUBLES * nsys, 0.0);
   for (int s = 0; s < nsys; ++s) {
@@ -277,14 +286,22 @@ nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<d
     hs[sh(SH_TOL, 0)] = tol[s];
     hs[CG_ASCALE] = ascale;
   }
-  ND_TRY_CUDA(c, cudaMemcpyAsync(states, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, c->stream));
-  ND_TRY_CUDA(c, cudaMemsetAsync(counters, 0, sizeof(unsigned) * nsys, c->stream));
-  ND_TRY_CUDA(c, cudaMemcpyAsync(p, b, fs * nsys, cudaMemcpyDeviceToDevice, c->stream));
-  ND_TRY_CUDA(c, cudaMemsetAsync(x, 0, fs * nsys, c->stream));
-  for (int s = 0; s < nsys; ++s)
-    ND_TRY_CUDA(c, blas_axpby(c->g, ps, r + s * fs, 1.0, static_cast<const char*>(b) + s * fs, 0.0, nullptr, true,
-                              slot(c, states + (size_t)s * CG_STATE_DOUBLES + CG_RR), c->stream));
-  ND_TRY_CUDA(c, bcg_init(states, nsys, c->stream));
+  ND_TRY_CUDA(c, cudaMemcpyAsync(states, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice, stream));
+  ND_TRY_CUDA(c, cudaMemsetAsync(counters, 0, sizeof(unsigned) * (nsys + 1), stream));
+  ND_TRY_CUDA(c, cudaMemcpyAsync(p, b, fs * nsys, cudaMemcpyDeviceToDevice, stream));
+  ND_TRY_CUDA(c, cudaMemsetAsync(x, 0, fs * nsys, stream));
+  for (int s = 0; s < nsys; ++s) {
+    ReduceSlot rs;
+    rs.partials = partials;
+    rs.counter = counters + nsys;
+    rs.result = states + (size_t)s * CG_STATE_DOUBLES + CG_RR;
+    ND_TRY_CUDA(c, blas_axpby(c->g, ps, r + s * fs, 1.0, static_cast<const char*>(b) + s * fs, 0.0, nullptr, true, rs,
+                              stream));
+  }
+  ND_TRY_CUDA(c, bcg_init(states, nsys, stream));
+  job->nsys = nsys;
+  job->states = states;
+  job->stream = stream;
   // graph: a device while-loop over the iterations, reused while the buffers are the same
   nd_ms_graph* G = nullptr;
   if (c->graphs_ok) {
@@ -341,26 +358,32 @@ nd_status bcg_run(nd_ctx* c, int ps, const void* b, void* x, const std::vector<d
       }
     }
   }
-  std::vector<double> hs((size_t)CG_STATE_DOUBLES * nsys);
   if (G) {
-    ND_TRY_CUDA(c, cudaGraphLaunch(G->exec, c->stream));
-    ND_TRY(read_back(c, states, hs.data(), (int)hs.size()));
-  } else {
-    int chunk = 8;
-    for (;;) {
-      for (int k = 0; k < chunk; ++k)
-        ND_TRY_CUDA(c, bcg_iteration(c, c->stream, ps, r, t, p, static_cast<char*>(x), fs, states, partials, counters,
-                                     nsys, maxit, nullptr));
-      ND_TRY(read_back(c, states, hs.data(), (int)hs.size()));
-      bool all = true;
-      for (int s = 0; s < nsys; ++s) {
-        const double* q = hs.data() + (size_t)s * CG_STATE_DOUBLES;
-        if (q[CG_DONE] == 0.0 && q[CG_PENDING] == 0.0) all = false;
-      }
-      if (all) break;
-      chunk = std::min(chunk * 2, 64);
-    }
+    ND_TRY_CUDA(c, cudaGraphLaunch(G->exec, stream));
+    return ND_OK;
   }
+  std::vector<double> hs((size_t)CG_STATE_DOUBLES * nsys);
+  int chunk = 8;
+  for (;;) {
+    for (int k = 0; k < chunk; ++k)
+      ND_TRY_CUDA(c, bcg_iteration(c, stream, ps, r, t, p, static_cast<char*>(x), fs, states, partials, counters, nsys,
+                                   maxit, nullptr));
+    ND_TRY(read_back_on(c, stream, states, hs.data(), (int)hs.size()));
+    bool all = true;
+    for (int s = 0; s < nsys; ++s) {
+      const double* q = hs.data() + (size_t)s * CG_STATE_DOUBLES;
+      if (q[CG_DONE] == 0.0 && q[CG_PENDING] == 0.0) all = false;
+    }
+    if (all) break;
+    chunk = std::min(chunk * 2, 64);
+  }
+  return ND_OK;
+}
+
+nd_status bcg_finish(nd_ctx* c, BcgJob* job, std::vector<int>* iters) {
+  const int nsys = job->nsys;
+  std::vector<double> hs((size_t)CG_STATE_DOUBLES * nsys);
+  ND_TRY(read_back_on(c, job->stream, job->states, hs.data(), (int)hs.size()));
   if (iters) iters->assign(nsys, 0);
   for (int s = 0; s < nsys; ++s) {
     const double* q = hs.data() + (size_t)s * CG_STATE_DOUBLES;
@@ -431,7 +454,7 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   auto ms_since = [](std::chrono::steady_clock::time_point t) {
     return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t).count();
   };
-  double t_res = 0.0, t_bcg = 0.0, t_upd = 0.0;
+  double t_res = 0.0, t_bcg = 0.0;
   auto t0 = now();
   MsResult ms;
   nd_status s = mscg_run(c, ps, 1, false, bS, x32, sigma, tol_s, {}, ascale, maxit, &ms);
@@ -464,7 +487,7 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   // per-shift reduction asked of a correction solve; raised tenfold (up to 1e-2) after a correction
   // that ran into its iteration cap: an FP32 CG resolves relative reductions down to about
   // u_32 kappa, which the lowest shifts of a deflated system only just clear
-  std::vector<double> tin(n, floor_in), rnorm(n, 1.0), h(3 * CG_NMAX, 0.0);
+  std::vector<double> tin(n, floor_in), rnorm(n, 1.0), h(3 * CG_NMAX, 0.0), tol_p(n, 1.0);
   std::vector<int> outer(n, 0), flat(n, 0);
   std::vector<bool> done(n, false);
   // a correction asks for a modest reduction; needing many more iterations than the sloppy pass
@@ -472,9 +495,12 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
   // the captured graph is keyed by the limit)
   int cap = 128;
   while (cap < 8 * st->iters + 100) cap *= 2;
-  for (int sweep = 0;; ++sweep) {
+  const int bmax = std::min(maxit, cap);
+  // FP64 residuals of the open shifts in [lo, hi) on the context's stream, their norms read back
+  // once; sets tol_p and *npend (the shifts that need another correction)
+  auto residual_sweep = [&](int lo, int hi, int* npend) -> nd_status {
     auto tr = now();
-    for (int l = 0; l < n; ++l) {
+    for (int l = lo; l < hi; ++l) {
       if (done[l]) continue;
       // r = b - (ascale Q^2 + sigma_l) x_l in FP64, ||r||^2 -> nrm[l]; R32_l = r / ||r||
       ND_TRY(residual64_dev(c, r64, b64, X64 + l * f64, sigma[l], ascale, nrm + 2 * l));
@@ -487,10 +513,9 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
     }
     ND_TRY(read_back(c, nrm, h.data(), 3 * CG_NMAX));
     if (trace) t_res += ms_since(tr);
-    std::vector<double> sig_p(n), tol_p(n, 1.0);
-    int npend = 0;
-    for (int l = 0; l < n; ++l) {
-      sig_p[l] = sigma[l];
+    *npend = 0;
+    for (int l = lo; l < hi; ++l) {
+      tol_p[l] = 1.0;
       if (done[l]) continue;
       rel[l] = std::sqrt(h[2 * l] / bnorm2);
       if (first[l] < 0) first[l] = rel[l];
@@ -518,41 +543,92 @@ nd_status mixed_solve_impl(nd_ctx* c, int ps, const void* b64, double bnorm2, co
       } else {
         rnorm[l] = rel[l] * bnorm;
         tol_p[l] = std::max(0.3 * tol[l] / rel[l], tin[l]);
-        ++npend;
+        ++*npend;
       }
       // a shift that is done takes part in the batched solve with a zero source (it stops at once)
       if (done[l]) ND_TRY_CUDA(c, cudaMemsetAsync(R32 + l * f32, 0, f32, c->stream));
     }
-    if (npend == 0) {
-      st->refine_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_refine).count();
-      break;
-    }
-    if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
-    std::vector<int> it;
-    auto tb = now();
-    s = bcg_run(c, 1, R32, E32, sig_p, tol_p, ascale, std::min(maxit, cap), &it);
-    if (s != ND_OK) return s;
-    if (trace) {
-      const double dt = ms_since(tb);
-      t_bcg += dt;
-      std::fprintf(stderr, "mixed solve: sweep %d, %d systems, batched CG max %d iterations %.2f ms\n", sweep, npend,
-                   *std::max_element(it.begin(), it.end()), dt);
-    }
-    auto tu = now();
-    for (int l = 0; l < n; ++l) {
+    return ND_OK;
+  };
+  // the correction solves of [lo, hi) as one batched CG on stream stx
+  auto correct_start = [&](int lo, int hi, const char* tag, cudaStream_t stx, BcgJob* job) -> nd_status {
+    const std::vector<double> sg(sigma.begin() + lo, sigma.begin() + hi), tp(tol_p.begin() + lo, tol_p.begin() + hi);
+    return bcg_start(c, 1, R32 + lo * f32, E32 + lo * f32, sg, tp, ascale, bmax, tag, stx, job);
+  };
+  // x_l += ||r_l|| e_l in FP64 for the open shifts of [lo, hi), after their correction solve
+  auto correct_apply = [&](int lo, int hi, const std::vector<int>& it) -> nd_status {
+    for (int l = lo; l < hi; ++l) {
       if (done[l]) continue;
-      st->sloppy_iters += it[l];
-      st->correction_iters += it[l];
-      if (it[l] >= std::min(maxit, cap)) tin[l] = std::min(10.0 * tin[l], 1e-2);
+      st->sloppy_iters += it[l - lo];
+      st->correction_iters += it[l - lo];
+      if (it[l - lo] >= bmax) tin[l] = std::min(10.0 * tin[l], 1e-2);
       ++outer[l];
-      // x_l += ||r_l|| e_l in FP64
       ND_TRY_CUDA(c, blas_axpy_widen(c->g, X64 + l * f64, rnorm[l], E32 + l * f32, c->stream));
     }
-    if (trace) t_upd += ms_since(tu);
+    return ND_OK;
+  };
+  // sweeps of residuals and corrections over [lo, hi) on the context's stream until every shift there
+  // meets its target
+  auto refine = [&](int lo, int hi, const char* tag) -> nd_status {
+    for (int sweep = 0;; ++sweep) {
+      int npend = 0;
+      ND_TRY(residual_sweep(lo, hi, &npend));
+      if (npend == 0) return ND_OK;
+      if (sweep >= 60) return fail(c, ND_ERR_NOT_CONVERGED, "mixed solve: defect correction did not converge");
+      auto tb = now();
+      BcgJob job;
+      std::vector<int> it;
+      ND_TRY(correct_start(lo, hi, tag, c->stream, &job));
+      ND_TRY(bcg_finish(c, &job, &it));
+      if (trace) {
+        const double dt = ms_since(tb);
+        t_bcg += dt;
+        std::fprintf(stderr, "mixed solve: shifts [%d, %d) sweep %d, %d systems, batched CG max %d iterations %.2f ms\n",
+                     lo, hi, sweep, npend, *std::max_element(it.begin(), it.end()), dt);
+      }
+      ND_TRY(correct_apply(lo, hi, it));
+    }
+  };
+  // The lowest shifts need the longest correction solves (the condition number of A + sigma grows as
+  // sigma falls), and on a small lattice their lockstep tail leaves the GPU mostly idle.  So the lowest
+  // third starts its first correction on a second stream, the other shifts are refined meanwhile on
+  // the context's stream (their FP64 residuals and correction solves fill the idle time), and then the
+  // lowest third is refined to the end.  Without CUDA graphs the batched CG is driven from the host
+  // and nothing overlaps, so the split is skipped.
+  // ND_MIXED_LOW in the environment sets the number of shifts in the low group (tuning)
+  int ks = (c->graphs_ok && n >= 6) ? (n + 2) / 3 : 0;
+  if (const char* e = std::getenv("ND_MIXED_LOW")) ks = (c->graphs_ok && n >= 2) ? std::max(0, std::min(n - 1, std::atoi(e))) : 0;
+  if (ks > 0) {
+    if (!c->aux_stream) ND_TRY_CUDA(c, cudaStreamCreateWithFlags(&c->aux_stream, cudaStreamNonBlocking));
+    if (!c->fork_ev) ND_TRY_CUDA(c, cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming));
+    if (!c->join_ev) ND_TRY_CUDA(c, cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming));
+    int npend = 0;
+    ND_TRY(residual_sweep(0, ks, &npend));
+    BcgJob job;
+    if (npend > 0) {
+      ND_TRY_CUDA(c, cudaEventRecord(c->fork_ev, c->stream));
+      ND_TRY_CUDA(c, cudaStreamWaitEvent(c->aux_stream, c->fork_ev, 0));
+      ND_TRY(correct_start(0, ks, "bc_low", c->aux_stream, &job));
+    }
+    ND_TRY(refine(ks, n, "bc_high"));
+    if (npend > 0) {
+      std::vector<int> it;
+      ND_TRY(bcg_finish(c, &job, &it));
+      ND_TRY_CUDA(c, cudaEventRecord(c->join_ev, c->aux_stream));
+      ND_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->join_ev, 0));
+      if (trace)
+        std::fprintf(stderr, "mixed solve: shifts [0, %d) first correction (second stream) max %d iterations\n", ks,
+                     *std::max_element(it.begin(), it.end()));
+      ND_TRY(correct_apply(0, ks, it));
+    }
+    ND_TRY(refine(0, ks, "bc_low"));
+  } else {
+    ND_TRY(refine(0, n, "bc_all"));
   }
+  st->refine_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_refine).count();
   if (trace)
-    std::fprintf(stderr, "mixed solve: FP64 residuals %.2f ms, batched CG %.2f ms, updates %.2f ms, total %.2f ms\n",
-                 t_res, t_bcg, t_upd, ms_since(t0));
+    std::fprintf(stderr, "mixed solve: FP64 residuals %.2f ms, batched CG %.2f ms, total %.2f ms\n", t_res, t_bcg,
+                 ms_since(t0));
   for (int l = 0; l < n; ++l) {
     if (std::getenv("ND_TRACE"))
       std::fprintf(stderr, "mixed solve: shift %d sigma %.3e sloppy resid %.3e outer %d final %.3e\n", l, sigma[l],

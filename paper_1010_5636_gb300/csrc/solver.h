@@ -1,5 +1,6 @@
 // Host-side building blocks shared by the solver, low-mode and overlap entry points.
 #pragma once
+#include <string>
 #include <vector>
 
 #include "ctx.h"
@@ -15,8 +16,16 @@ nd_status q_apply(nd_ctx* c, int prec, void* out, const void* in, double a = 1.0
 // Device buffer for one internal field of `prec`, cached under `name`.
 void* field(nd_ctx* c, const char* name, int prec, int count = 1);
 
-// Read n doubles from device memory (synchronises the stream).
+// Read n doubles from device memory (synchronises the context's stream, or st).
 nd_status read_back(nd_ctx* c, const double* dev, double* host, int n);
+nd_status read_back_on(nd_ctx* c, cudaStream_t st, const double* dev, double* host, int n);
+
+// A batched CG in flight (solver.cu, bcg_start / bcg_finish).
+struct BcgJob {
+  int nsys = 0;
+  double* states = nullptr;
+  cudaStream_t stream = nullptr;
+};
 
 struct MsResult {
   int iters = 0;
