@@ -877,8 +877,8 @@ def main():
     peaks, src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = d["per_launch_bytes"] / (d["avg_launch_ms"] * 1e-3) / 1e9
-    # DRAM bytes of one launch from the committed ncu capture of this kernel (24^3x48 case scaled
-    # to this lattice by the number of sites); null if the summary is missing
+    # DRAM bytes of one launch of this kernel on this lattice, from the committed ncu capture
+    # (dram__bytes_read.sum + dram__bytes_write.sum); null if the summary is missing
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "dslash_hop_24x48_fp32r12.md")
     if os.path.exists(tfile):

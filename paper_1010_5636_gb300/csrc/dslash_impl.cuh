@@ -144,16 +144,7 @@ __device__ __forceinline__ void q_site_pairs(const Geom& g, const QLaunch& A, co
   if (act) {
     const Site s = site_of(g, p, h);
     Spinor2 acc;
-    zero2(acc);
-    const char* L = static_cast<const char*>(A.links);
-    hop2<P, R, 0, true>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 0, false>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 1, true>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 1, false>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 2, true>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 2, false>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 3, true>(acc, g, s, p, h, L, A.in);
-    hop2<P, R, 3, false>(acc, g, s, p, h, L, A.in);
+    hopping_sum2<P, R>(acc, g, s, p, h, static_cast<const char*>(A.links), A.in);
     const bool rd = REDUCE || A.diag != 0.0;
     if constexpr (BASE != Q_PLAIN) {
       if (rd)
