@@ -90,7 +90,12 @@ size_t nd_spinor_bytes(const nd_ctx* ctx, nd_prec prec);
 nd_status nd_set_links(nd_ctx* ctx, const double* U_dev, const int recon[3]);
 
 /* Canonical FP64 spinors (nrhs consecutive fields, device) <-> internal layout of precision
- * prec (nrhs consecutive fields of nd_spinor_bytes each, device). */
+ * prec (nrhs consecutive fields of nd_spinor_bytes each, device).  The internal layout is the
+ * library's own and may change: the whole lattice, even-odd ordered (parity-0 block first), as a
+ * structure of arrays of 16-byte chunks, chunk c of site h of parity p at index (p * NC + c) * V/2 + h;
+ * FP64 keeps the canonical component order (NC = 12), FP32 (NC = 6) and FP16 (NC = 3, then one FP32
+ * scale per site) hold the components as spin-row pairs (s0, s1) and (s2, s3) of each colour's real
+ * and imaginary parts, the operands of packed FP32 arithmetic. */
 nd_status nd_pack_spinor(nd_ctx* ctx, void* internal_dev, const double* canon_dev, nd_prec prec, int nrhs);
 nd_status nd_unpack_spinor(nd_ctx* ctx, double* canon_dev, const void* internal_dev, nd_prec prec, int nrhs);
 
