@@ -225,30 +225,54 @@ __device__ __forceinline__ void hop2_compute(Spinor2& acc, const HopOperands<P, 
   spin_accumulate2<MU, FWD>(acc, cr, ci);
 }
 
-// The eight packed hops with the operands of the next hop requested before the current hop's
-// arithmetic (two operand sets in flight), in the order of hopping_sum.  The same arithmetic as
-// loading and computing each hop in turn, bit for bit; written this way the scheduler keeps two
-// hops' loads in flight, which measured 4 % faster on the one-parity hop (64x32^3, 96.0 against
-// 100.1 us back to back).
+// The eight packed hops with the operands of the hops two and three ahead requested before the
+// current hop's arithmetic (three operand sets rotating), in the order of hopping_sum.  The same
+// arithmetic as loading and computing each hop in turn, bit for bit; written this way the
+// scheduler keeps the loads of later hops in flight while a hop computes.  Measured on 64x32^3 back
+// to back, one-parity hop: 96.5 us with every hop loaded just before its arithmetic, 96.0 us with one
+// hop ahead, 94.5 us with two (full Q 157.8 / 156.7 / 155.3 us), all at 128 registers.
 template <int P, int R>
 __device__ __forceinline__ void hopping_sum2(Spinor2& acc, const Geom& g, const Site& s, int p, int h,
                                              const char* L, const void* in) {
   zero2(acc);
-  HopOperands<P, R> a, b;
+  if constexpr (R == 8 || P == P16) {
+    // one hop ahead: the 8-real rebuild needs the registers (three sets spilled ~200 bytes), and
+    // FP16, bound by instruction issue, measured 5 % slower with three sets (64x32^3, flushed:
+    // 12-real hop 84.6 against 80.5 us)
+    HopOperands<P, R> a, b;
+    hop2_load<P, R, 0, true>(a, g, s, p, h, L, in);
+    hop2_load<P, R, 0, false>(b, g, s, p, h, L, in);
+    hop2_compute<P, R, 0, true>(acc, a, g);
+    hop2_load<P, R, 1, true>(a, g, s, p, h, L, in);
+    hop2_compute<P, R, 0, false>(acc, b, g);
+    hop2_load<P, R, 1, false>(b, g, s, p, h, L, in);
+    hop2_compute<P, R, 1, true>(acc, a, g);
+    hop2_load<P, R, 2, true>(a, g, s, p, h, L, in);
+    hop2_compute<P, R, 1, false>(acc, b, g);
+    hop2_load<P, R, 2, false>(b, g, s, p, h, L, in);
+    hop2_compute<P, R, 2, true>(acc, a, g);
+    hop2_load<P, R, 3, true>(a, g, s, p, h, L, in);
+    hop2_compute<P, R, 2, false>(acc, b, g);
+    hop2_load<P, R, 3, false>(b, g, s, p, h, L, in);
+    hop2_compute<P, R, 3, true>(acc, a, g);
+    hop2_compute<P, R, 3, false>(acc, b, g);
+    return;
+  }
+  HopOperands<P, R> a, b, c;
   hop2_load<P, R, 0, true>(a, g, s, p, h, L, in);
   hop2_load<P, R, 0, false>(b, g, s, p, h, L, in);
+  hop2_load<P, R, 1, true>(c, g, s, p, h, L, in);
   hop2_compute<P, R, 0, true>(acc, a, g);
-  hop2_load<P, R, 1, true>(a, g, s, p, h, L, in);
+  hop2_load<P, R, 1, false>(a, g, s, p, h, L, in);
   hop2_compute<P, R, 0, false>(acc, b, g);
-  hop2_load<P, R, 1, false>(b, g, s, p, h, L, in);
-  hop2_compute<P, R, 1, true>(acc, a, g);
-  hop2_load<P, R, 2, true>(a, g, s, p, h, L, in);
-  hop2_compute<P, R, 1, false>(acc, b, g);
-  hop2_load<P, R, 2, false>(b, g, s, p, h, L, in);
-  hop2_compute<P, R, 2, true>(acc, a, g);
+  hop2_load<P, R, 2, true>(b, g, s, p, h, L, in);
+  hop2_compute<P, R, 1, true>(acc, c, g);
+  hop2_load<P, R, 2, false>(c, g, s, p, h, L, in);
+  hop2_compute<P, R, 1, false>(acc, a, g);
   hop2_load<P, R, 3, true>(a, g, s, p, h, L, in);
-  hop2_compute<P, R, 2, false>(acc, b, g);
+  hop2_compute<P, R, 2, true>(acc, b, g);
   hop2_load<P, R, 3, false>(b, g, s, p, h, L, in);
+  hop2_compute<P, R, 2, false>(acc, c, g);
   hop2_compute<P, R, 3, true>(acc, a, g);
   hop2_compute<P, R, 3, false>(acc, b, g);
 }

@@ -31,8 +31,11 @@ __device__ __forceinline__ void q_site(const Geom& g, const char* links, const v
   SpinorIO<P>::store(acc, out, g.Vh, p, h);
 }
 
+// FP64 needs its registers (about 250 per thread) and is bound by the FP64 pipe: 2 blocks per SM;
+// FP32 and FP16 run 8 blocks per SM (128 registers).
 template <int P, int R>
-__global__ void __launch_bounds__(BT_THREADS, 8) q_batched_kernel(const LatticeWork* work, int nlat, int total) {
+__global__ void __launch_bounds__(BT_THREADS, P == P64 ? 2 : 8) q_batched_kernel(const LatticeWork* work, int nlat,
+                                                                                 int total) {
   __shared__ int begin[ND_MAX_BATCH + 1];
   if (threadIdx.x <= nlat) begin[threadIdx.x] = threadIdx.x < nlat ? work[threadIdx.x].tile_begin : total;
   __syncthreads();
