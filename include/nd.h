@@ -74,6 +74,10 @@ typedef enum {
  * device is usable. */
 nd_status nd_create(nd_ctx** ctx, const int dims[4], int antiperiodic_t, double m, double s, void* stream);
 void nd_destroy(nd_ctx* ctx);
+/* Every call issues its work on the context's stream.  The mixed-precision refinement of a solve with
+ * six or more shifts (nd_solve, nd_apply_sign, nd_apply_DN, nd_propagator) also runs part of its work on
+ * a second stream that the context owns: forked from the context's stream with an event and joined back
+ * before the call returns, so the caller sees stream order as usual. */
 nd_status nd_set_stream(nd_ctx* ctx, void* stream);
 const char* nd_status_string(nd_status st);
 const char* nd_last_error(const nd_ctx* ctx);
