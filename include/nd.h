@@ -214,7 +214,7 @@ typedef struct {
  * until the residuals are small, then FP64; FP64 orthogonalisation and Rayleigh-Ritz of Q^2), then the
  * Rayleigh-Ritz eigenpairs (nu_k, u_k) of Q on their span, the residues rho_k and kappa_+- (Sec. 2.3).
  * The basis stays in the context for nd_apply_DN.  Host outputs (may be NULL):
- * nu[l], rho[l], eval_Q2[l+1] (the Lanczos eigenvalues of Q^2, ascending).
+ * nu[l], rho[l], eval_Q2[l+1] (the Rayleigh-Ritz values of Q^2 from the block, ascending).
  * Converges each of the l+1 lowest Ritz values of Q^2 to relative residual tol. */
 nd_status nd_lowmodes(nd_ctx* ctx, int l, double tol, int maxit, double* nu, double* rho, double* eval_Q2,
                       nd_lowmode_info* info);
